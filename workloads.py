@@ -1,0 +1,122 @@
+"""Seeded synthetic inputs for the Poisson-solve workloads.
+
+This module is shared by the tests, the bench and the oracle checks.  It holds
+input recipes only (random fields and the workload table); it contains none
+of the solver's arithmetic and imports neither the oracle nor the CUDA
+library.  All draws use numpy's PCG64 generator with a fixed seed.
+
+The paper measures on no public data set: its runs are 512^3 and 256^3 grids
+with periodic or staggered-Neumann conditions (Sec. 4) and a 16.3 M-cell
+urban flow model (Sec. 5).  The workloads below are synthetic stand-ins with
+the grid sizes and boundary-condition mixes of those runs.
+
+Boundary-condition codes: 0 periodic (P), 1 Dirichlet regular (DR),
+2 Dirichlet staggered (DS), 3 Neumann regular (NR), 4 Neumann staggered (NS).
+Approximation codes: 0 pseudo-spectral (Table 3), 1 second-order finite
+differences (Table 4).
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+P, DR, DS, NR, NS = 0, 1, 2, 3, 4
+SPECTRAL, FD2 = 0, 1
+
+
+def rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def uniform_meanfree(shape, seed, dtype=np.float64):
+    """i.i.d. U[-1, 1], arithmetic mean subtracted."""
+    g = rng(seed).uniform(-1.0, 1.0, size=shape)
+    g -= g.mean()
+    return g.astype(dtype)
+
+
+def normal_meanfree(shape, seed, dtype=np.float64):
+    """i.i.d. N(0, 1), arithmetic mean subtracted."""
+    g = rng(seed).standard_normal(size=shape, dtype=np.float64 if dtype == np.float64 else np.float32)
+    g = g.astype(np.float64 if dtype == np.float64 else np.float32)
+    g -= g.mean(dtype=np.float64)
+    return g.astype(dtype)
+
+
+def normal(shape, seed, dtype=np.float64):
+    """i.i.d. N(0, 1) (no mean removal)."""
+    g = rng(seed).standard_normal(size=shape, dtype=np.float64 if dtype == np.float64 else np.float32)
+    return g.astype(dtype)
+
+
+def smooth_random_field(shape, seed, slope=-3.0, noise=1e-3, dtype=np.float32):
+    """Gaussian random field with power spectrum ~ |k|^slope plus white noise.
+
+    White N(0,1) noise is filtered in Fourier space by |k|^(slope/2) (integer
+    wavenumbers, k = 0 removed), scaled to unit variance, then noise*N(0,1)
+    is added and the arithmetic mean subtracted.  Computed in FP32 slabs so
+    that 1024^3 fits in a few host copies of the field.
+    """
+    import scipy.fft as sf
+
+    gen = rng(seed)
+    f = gen.standard_normal(size=shape, dtype=np.float32)
+    spec = sf.rfftn(f, workers=-1)
+    del f
+    kk = [np.fft.fftfreq(n, 1.0 / n).astype(np.float32) for n in shape[:-1]]
+    kk.append(np.fft.rfftfreq(shape[-1], 1.0 / shape[-1]).astype(np.float32))
+    d = len(shape)
+    # filter slab by slab along the first axis to bound temporaries
+    tail = None
+    if d >= 2:
+        grids = np.meshgrid(*kk[1:], indexing="ij")
+        tail = sum(gk.astype(np.float32) ** 2 for gk in grids)
+        del grids
+    for i0 in range(shape[0]):
+        k2 = kk[0][i0] ** 2 + (tail if tail is not None else 0.0)
+        k2 = np.asarray(k2, dtype=np.float32)
+        with np.errstate(divide="ignore"):
+            amp = np.where(k2 > 0, k2 ** np.float32(slope / 4.0), np.float32(0.0))
+        spec[i0] *= amp
+    field = sf.irfftn(spec, s=shape, workers=-1).astype(np.float32)
+    del spec
+    field /= np.float32(field.std(dtype=np.float64))
+    field += np.float32(noise) * gen.standard_normal(size=shape, dtype=np.float32)
+    field -= np.float32(field.mean(dtype=np.float64))
+    return field.astype(dtype)
+
+
+# Workload table.  n = (nx, ny, nz) as in the C interface; arrays are numpy
+# shapes (nz, ny, nx), x fastest.
+WORKLOADS = {
+    # 32^3, periodic x,y,z, pseudo-spectral, FP64 on [0, 2 pi)^3
+    "p3_spectral_32_f64": dict(
+        n=(32, 32, 32), bcs=(P, P, P), Ls=(2 * math.pi,) * 3, approx=SPECTRAL,
+        dtype="f64", gen=("uniform_meanfree", 1)),
+    # 256^3 FP32 FD2, x periodic, y staggered Dirichlet, z staggered Neumann, dx = 1/256
+    "mixed_fd2_256_f32": dict(
+        n=(256, 256, 256), bcs=(P, DS, NS), Ls=(1.0, 1.0, 1.0), approx=FD2,
+        dtype="f32", gen=("normal_meanfree", 2)),
+    # 1024^3 FP32 FD2, periodic x,y, staggered Neumann z, L = 1 per axis
+    "ppn_fd2_1024_f32": dict(
+        n=(1024, 1024, 1024), bcs=(P, P, NS), Ls=(1.0, 1.0, 1.0), approx=FD2,
+        dtype="f32", gen=("smooth_random_field", 3)),
+}
+
+
+def make_input(name_or_spec, shape=None, dtype=None):
+    """Seeded right-hand side g for a workload (numpy array, shape (nz,ny,nx))."""
+    spec = WORKLOADS[name_or_spec] if isinstance(name_or_spec, str) else name_or_spec
+    nx, ny, nz = spec["n"]
+    shp = shape if shape is not None else (nz, ny, nx)
+    dt = dtype if dtype is not None else (np.float64 if spec["dtype"] == "f64" else np.float32)
+    kind, seed = spec["gen"]
+    if kind == "uniform_meanfree":
+        return uniform_meanfree(shp, seed, dt)
+    if kind == "normal_meanfree":
+        return normal_meanfree(shp, seed, dt)
+    if kind == "smooth_random_field":
+        return smooth_random_field(shp, seed, dtype=dt)
+    raise ValueError(kind)
