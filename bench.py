@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark of the direct FFT Poisson solve on GB300.
+
+One step = one full solve (x forward, y forward, z forward + eigenvalue
+divide + z backward, y backward, x backward) of the 1024^3 FP32 workload
+(periodic x, y; staggered Neumann z; second-order finite-difference
+eigenvalues; seeded smooth Gaussian random field + 1e-3 white noise).  The
+field (4 GiB) is far larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  `value` is grid points solved per second
+over all ranks, device-timed with CUDA events on the solve stream with the
+inputs resident in HBM; `e2e` is the same metric through
+poisfft_solve_host (host buffers; H2D + solve + D2H inside the timed
+region); `roofline` covers the launch with the largest share of the step
+time, timed live with per-launch CUDA events recorded by the library on the
+same stream; `cpu_baseline` is the FP64 oracle on a bounded sample of the
+same workload on this machine's host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--impl ours|reference] [--no-check]
+
+Multi-GPU (torchrun): every rank solves its own replica of the workload (the
+solve has no cross-GPU exchange in this build), the step time is the max over
+ranks and `value` counts all ranks' points ("scaling": "weak").
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "3D solve grid-pts/s & HBM-roofline fraction at 256^3/1024^3; max err vs FP64"
+UNIT = "grid-pts/s"
+DEFAULT_WORKLOAD = "ppn_fd2_1024_f32"
+BC_NAME = {0: "P", 1: "DR", 2: "DS", 3: "NR", 4: "NS"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(W.WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-check", action="store_true", help="skip the FP64 error check of the solution")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_sample_oracle(spec, budget_s=12.0):
+    """Time the FP64 oracle (dense Table 1 matrices) on the largest cubic
+    sample of the workload's BC set that fits the time budget."""
+    from oracle import poisson as O
+
+    bcs, Ls, approx = spec["bcs"], spec["Ls"], spec["approx"]
+    n = 32
+    best = None
+    while True:
+        g = W.normal((n, n, n), 99, dtype=np.float64)
+        t0 = time.perf_counter()
+        O.solve(g, bcs, Ls, approx)
+        dt = time.perf_counter() - t0
+        best = (n, dt)
+        if dt > budget_s / 8 or n >= 256:
+            break
+        n *= 2
+    n, dt = best
+    return {"value": n ** 3 / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"FP64 oracle (dense Table-1 matrices, numpy/BLAS) on a {n}^3 grid with the workload's "
+                      f"BCs {tuple(BC_NAME[b] for b in bcs)} and eigenvalues; {dt:.2f} s per solve"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import poisson as O
+
+    spec = W.WORKLOADS[args.workload]
+    bcs, Ls, approx = spec["bcs"], spec["Ls"], spec["approx"]
+    # bounded sample of the workload: a cubic sub-grid sized for ~10 s per step
+    n = 64
+    g = W.normal((n, n, n), 5, dtype=np.float64)
+    t0 = time.perf_counter()
+    O.solve(g, bcs, Ls, approx)
+    dt = time.perf_counter() - t0
+    while dt < 1.5 and n < 256:
+        n *= 2
+        g = W.normal((n, n, n), 5, dtype=np.float64)
+        t0 = time.perf_counter()
+        O.solve(g, bcs, Ls, approx)
+        dt = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        O.solve(g, bcs, Ls, approx)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.solve(g, bcs, Ls, approx)
+    total = time.perf_counter() - t0
+    value = n ** 3 * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args.workload, spec),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": f"FP64 oracle (dense Table-1 matrices) on a {n}^3 sub-grid with the workload's "
+                                   f"BCs and eigenvalues, per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(name, spec):
+    nx, ny, nz = spec["n"]
+    return {"workload": name, "n": [nx, ny, nz], "bcs": [BC_NAME[b] for b in spec["bcs"]],
+            "approx": "spectral" if spec["approx"] == 0 else "fd2", "L": list(spec["Ls"]),
+            "l2": "inputs larger than L2 (no flush needed)" if nx * ny * nz * 4 > 129e6 else "inputs smaller than L2, not flushed (not a headline workload)"}
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1409_8116_gb300 import binding as pb
+
+    spec = W.WORKLOADS[args.workload]
+    nx, ny, nz = spec["n"]
+    npts = nx * ny * nz
+    f64 = spec["dtype"] == "f64"
+    tdt = torch.float64 if f64 else torch.float32
+    esize = 8 if f64 else 4
+
+    g_host = W.make_input(spec)
+    plan = pb.Plan(spec["n"], spec["Ls"], spec["bcs"], spec["approx"], pb.F64 if f64 else pb.F32)
+    launches = plan.launches()
+    stream = torch.cuda.Stream()
+    g = torch.from_numpy(g_host).to("cuda")
+    phi = torch.empty_like(g)
+    torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            plan.solve(phi, g, stream)
+    stream.synchronize()
+    assert plan.check(stream) == pb.OK
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    # ---- timed region: K solves, per-launch events recorded by the library
+    plan.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.solve(phi, g, stream)
+    e1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    plan.profile(False)
+    ms_total = e0.elapsed_time(e1)
+    per_launch_ms, nsolves = plan.profile_read()
+    assert plan.check(stream) == pb.OK
+    t_local = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    value = world * npts * args.steps / (ms_max / 1e3)
+
+    # dominant launch: largest share of the step time
+    shares = [t / sum(per_launch_ms) for t in per_launch_ms]
+    dom = int(np.argmax(per_launch_ms))
+    dom_ms = per_launch_ms[dom] / nsolves
+    peak, peak_kind = load_peaks()
+    achieved = launches[dom]["bytes"] / (dom_ms / 1e3) / 1e9
+    per_launch = [dict(launches[i], ms=per_launch_ms[i] / nsolves, share=shares[i],
+                       gbs=launches[i]["bytes"] / (per_launch_ms[i] / nsolves / 1e3) / 1e9)
+                  for i in range(len(launches))]
+    step_bytes = sum(l["bytes"] for l in launches)
+
+    # ---- end to end through the host-buffer entry point
+    gh = torch.from_numpy(g_host).pin_memory()
+    ph = torch.empty_like(gh).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        plan.solve_host(ph, gh, stream)
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.solve_host(ph, gh, stream)
+    t_e2e = time.perf_counter() - t0
+    t_e2e_t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.all_reduce(t_e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * npts * e2e_steps / float(t_e2e_t.item())
+
+    # ---- accuracy against the FP64 oracle (not timed)
+    err = None
+    if not args.no_check and rank == 0:
+        from oracle import poisson as O
+
+        ref = O.solve(g_host.astype(np.float64), spec["bcs"], spec["Ls"], spec["approx"],
+                      method="dense" if npts <= 64 ** 3 else "fft")
+        err = O.rel_max_error(phi.cpu().numpy().astype(np.float64), ref)
+        del ref
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_sample_oracle(spec)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if f64 else "f32", "data": "synthetic",
+            "config": workload_config(args.workload, spec),
+            "max_rel_err_vs_fp64": err,
+            "hbm_frac_step": step_bytes * args.steps / (ms_max / 1e3) / 1e9 / peak,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": f"{launches[dom]['kernel']} ({launches[dom]['mode']}, axis {launches[dom]['axis']})",
+                         "peak_source": f"{peak_kind} hbm_gbs"},
+            "launches": per_launch,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": npts * esize,
+                    "d2h_bytes_per_step": npts * esize},
+            "gpu_launches": len(launches) * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,143 @@
+/*
+ * poisfft.h -- C interface of the GB300 (sm_103a) fast Poisson solver.
+ *
+ * Solves the discrete Poisson equation lap(phi) = g (Eq. poisson-continuous,
+ * Sec. 1) on a uniform 1-, 2- or 3-D grid by the three-step algorithm of
+ * Sec. 2.1: forward transform along every axis chosen by that axis's
+ * boundary condition (Table 2), division by the Laplacian eigenvalues
+ * (Table 3 pseudo-spectral or Table 4 second-order finite differences,
+ * summed over axes as in Sec. 2.3), and the backward transforms (Table 2).
+ * The paper's library exposes the same three calls: initialise the solver,
+ * compute, finalise (Sec. 3).
+ *
+ * Array layout everywhere: x fastest.  Element (i, j, k) of an nx*ny*nz
+ * field is at offset i + nx*(j + ny*k), i.e. a C array [nz][ny][nx].
+ *
+ * Every call returns a status code: POISFFT_OK (0) or a negative error.
+ * No call aborts the process.
+ */
+#ifndef POISFFT_H
+#define POISFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Boundary conditions of one face (Sec. 2.1 grids, Table 2 rows).
+ *   POISFFT_P   periodic, regular grid x_j = j L/n                (DFT / IDFT)
+ *   POISFFT_DR  Dirichlet, regular grid x_j = (j+1) L/(n+1)       (DST-I)
+ *   POISFFT_DS  Dirichlet, staggered grid x_j = (j+1/2) L/n       (DST-II / DST-III)
+ *   POISFFT_NR  Neumann, regular grid x_j = j L/(n-1)             (DCT-I)
+ *   POISFFT_NS  Neumann, staggered grid x_j = (j+1/2) L/n         (DCT-II / DCT-III) */
+typedef enum { POISFFT_P = 0, POISFFT_DR = 1, POISFFT_DS = 2, POISFFT_NR = 3, POISFFT_NS = 4 } poisfft_bc;
+
+/* Eigenvalue set: Table 3 (pseudo-spectral) or Table 4 (2nd-order FD). */
+typedef enum { POISFFT_SPECTRAL = 0, POISFFT_FD2 = 1 } poisfft_approx;
+
+/* Storage and arithmetic type of phi and g.  The paper's library offers single
+ * and double precision solver objects (Sec. 3).  F32: float arrays, FP32
+ * arithmetic with tables rounded once from FP64.  F64: double arrays and
+ * arithmetic. */
+typedef enum { POISFFT_F32 = 0, POISFFT_F64 = 1 } poisfft_dtype;
+
+/* Status codes. */
+enum {
+  POISFFT_OK = 0,
+  POISFFT_ERR_INVALID_ARG = -1,     /* null pointer, dims outside 1..3, n < 1, L <= 0, bad enum */
+  POISFFT_ERR_UNSUPPORTED_BC = -2,  /* the two faces of an axis differ, or periodic paired with non-periodic */
+  POISFFT_ERR_UNSUPPORTED_SIZE = -3,/* an axis length the kernels cannot tile (reported, never truncated) */
+  POISFFT_ERR_ALLOC = -4,           /* device or host allocation failed; nothing is leaked */
+  POISFFT_ERR_CUDA = -5,            /* a CUDA runtime/driver call failed (no device, launch error, ...) */
+  POISFFT_ERR_MISALIGNED = -6,      /* phi or g not aligned to the element size */
+  POISFFT_ERR_TIMEOUT = -7,         /* a bounded device wait gave up (error flag set by a kernel) */
+  POISFFT_ERR_NOT_IMPLEMENTED = -8  /* valid arguments outside what this build implements */
+};
+
+typedef struct poisfft_plan poisfft_plan;  /* opaque; owned by the library */
+
+/* Create a solver for one grid.
+ *   out    : receives the plan (set to NULL on error).
+ *   dims   : 1, 2 or 3 (Sec. 3: 1, 2 and 3 dimensions).
+ *   n      : n[0..dims-1] = points along x, y, z.  n >= 1; NR needs n >= 2.
+ *   L      : L[0..dims-1] = domain lengths; dx per axis follows the grid of
+ *            the axis's BC (L/n for P and staggered, L/(n+1) DR, L/(n-1) NR).
+ *   bc     : bc[2*a] and bc[2*a+1] = the two faces of axis a (low, high).
+ *            Both faces must be equal (the transforms of Table 2 are defined
+ *            per axis); every per-axis combination is accepted.
+ *   approx : poisfft_approx.   dtype : poisfft_dtype.
+ * Allocates the device workspace (about one field of the plan's dtype plus
+ * padding) and FP64-derived tables on the current CUDA device.  All
+ * argument checks happen before any CUDA call, so argument errors are
+ * reported even without a GPU. */
+int poisfft_plan_create(poisfft_plan** out, int dims, const int64_t n[], const double L[],
+                        const int bc[], int approx, int dtype);
+
+/* Solve lap(phi) = g on the plan's grid (Sec. 2.1 algorithm).
+ *   phi, g : device pointers to dense x-fastest arrays of n[0]*n[1]*n[2]
+ *            elements of the plan's dtype, aligned to the element size.
+ *            g is only read.  phi == g (in place) is allowed; any other
+ *            overlap is not.
+ *   stream : a cudaStream_t (NULL = legacy default stream).
+ * Asynchronous: returns after enqueueing the kernels on `stream`.  A plan
+ * owns one workspace, so one plan must not run on two streams at once.
+ * For singular problems (every axis P, NR or NS) the component of g in the
+ * null space is removed (the all-zero spectral coefficient is set to 0), so
+ * phi has zero mean (trapezoid-weighted along NR axes). */
+int poisfft_solve(poisfft_plan* plan, void* phi, const void* g, void* stream);
+
+/* The same solve from and to HOST memory: copies g to the device, solves,
+ * copies phi back, all on `stream`, then synchronises the stream.  Pinned
+ * host buffers give full copy bandwidth; pageable ones work too.  Device
+ * staging buffers (two fields) are allocated on first use and kept by the
+ * plan until poisfft_destroy. */
+int poisfft_solve_host(poisfft_plan* plan, void* phi_host, const void* g_host, void* stream);
+
+/* Read and clear the plan's device error flag (bounded waits in the kernels
+ * set it instead of hanging).  Synchronises `stream`.  Returns POISFFT_OK,
+ * POISFFT_ERR_TIMEOUT or POISFFT_ERR_CUDA. */
+int poisfft_check(poisfft_plan* plan, void* stream);
+
+/* Release the plan's device memory and tables.  NULL is a no-op.  The caller
+ * must make sure no solve on the plan is still running. */
+int poisfft_destroy(poisfft_plan* plan);
+
+/* Static description of a status code (never NULL). */
+const char* poisfft_status_string(int status);
+
+/* Plan introspection for benchmarks and tests (host only, no CUDA calls).
+ *   info[0] = number of kernel launches per solve
+ *   info[1] = workspace bytes
+ *   info[2] = bytes of the dominant (largest-traffic) sweep's algorithmic
+ *             HBM traffic per launch: read + write of its tile data
+ *   info[3] = index (0-based, launch order) of that sweep
+ * Returns POISFFT_OK or POISFFT_ERR_INVALID_ARG. */
+int poisfft_plan_info(const poisfft_plan* plan, int64_t info[4]);
+
+/* Per-launch timing for benchmarks (no paper counterpart; measurement aid).
+ * When enabled, every solve records a CUDA event on its stream before each
+ * kernel launch and after the last one.  Host cost: one event record per
+ * launch.  Returns POISFFT_OK or POISFFT_ERR_INVALID_ARG. */
+int poisfft_profile_enable(poisfft_plan* plan, int enable);
+
+/* Synchronise the recorded events and return, per launch position i of a
+ * solve, the summed device milliseconds over all profiled solves since the
+ * last call: ms[i] for i < min(cap, *nlaunch).  *nsolves = number of
+ * profiled solves.  Clears the record.  POISFFT_ERR_CUDA on event errors. */
+int poisfft_profile_read(poisfft_plan* plan, double* ms, int cap, int* nlaunch, int* nsolves);
+
+/* Description of launch position i of a solve (host only).
+ *   out[0] = algorithmic HBM bytes of the launch (reads + writes of its data)
+ *   out[1] = kernel: 0 contiguous (x) sweep, 1 strided (y/z) sweep
+ *   out[2] = mode: 0 forward, 1 backward, 2 forward + divide + backward
+ *   out[3] = axis: 0 x, 1 y, 2 z
+ * Returns POISFFT_OK or POISFFT_ERR_INVALID_ARG (i out of range). */
+int poisfft_launch_info(const poisfft_plan* plan, int i, int64_t out[4]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POISFFT_H */

@@ -1,0 +1,227 @@
+"""Thin ctypes binding of libpoisfft.so (argument marshalling only).
+
+Every call goes through the C interface declared in include/poisfft.h; all
+arithmetic of the solve runs in the library's CUDA kernels.  PyTorch is used
+only by callers that want device tensors and streams; the functions here take
+raw pointers (ints) or torch tensors and pass their addresses.
+
+If the shared library is missing the import of this module fails loudly --
+there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpoisfft.so")
+
+P, DR, DS, NR, NS = 0, 1, 2, 3, 4
+SPECTRAL, FD2 = 0, 1
+F32, F64 = 0, 1
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_UNSUPPORTED_BC = -2
+ERR_UNSUPPORTED_SIZE = -3
+ERR_ALLOC = -4
+ERR_CUDA = -5
+ERR_MISALIGNED = -6
+ERR_TIMEOUT = -7
+ERR_NOT_IMPLEMENTED = -8
+
+EXPORTED = [
+    "poisfft_plan_create",
+    "poisfft_solve",
+    "poisfft_solve_host",
+    "poisfft_check",
+    "poisfft_destroy",
+    "poisfft_status_string",
+    "poisfft_plan_info",
+    "poisfft_profile_enable",
+    "poisfft_profile_read",
+    "poisfft_launch_info",
+]
+
+
+class PoisFFTError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    lib.poisfft_plan_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, i64p,
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.c_int, ctypes.c_int]
+    lib.poisfft_plan_create.restype = ctypes.c_int
+    lib.poisfft_solve.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.poisfft_solve.restype = ctypes.c_int
+    lib.poisfft_solve_host.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.poisfft_solve_host.restype = ctypes.c_int
+    lib.poisfft_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.poisfft_check.restype = ctypes.c_int
+    lib.poisfft_destroy.argtypes = [ctypes.c_void_p]
+    lib.poisfft_destroy.restype = ctypes.c_int
+    lib.poisfft_status_string.argtypes = [ctypes.c_int]
+    lib.poisfft_status_string.restype = ctypes.c_char_p
+    lib.poisfft_plan_info.argtypes = [ctypes.c_void_p, i64p]
+    lib.poisfft_plan_info.restype = ctypes.c_int
+    lib.poisfft_profile_enable.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.poisfft_profile_enable.restype = ctypes.c_int
+    lib.poisfft_profile_read.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.poisfft_profile_read.restype = ctypes.c_int
+    lib.poisfft_launch_info.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p]
+    lib.poisfft_launch_info.restype = ctypes.c_int
+    return lib
+
+
+lib = _load()
+
+
+def status_string(status: int) -> str:
+    return lib.poisfft_status_string(int(status)).decode()
+
+
+def plan_create(n, L, bc, approx, dtype):
+    """Create a plan.  n, L: per-axis sequences (x first).  bc: per-axis codes
+    (one per axis, used for both faces) or 2*dims face codes."""
+    dims = len(n)
+    if len(bc) == dims:
+        faces = [b for b in bc for _ in (0, 1)]
+    else:
+        faces = list(bc)
+    plan = ctypes.c_void_p()
+    n_arr = (ctypes.c_int64 * max(dims, 1))(*[int(v) for v in n])
+    L_arr = (ctypes.c_double * max(dims, 1))(*[float(v) for v in L])
+    bc_arr = (ctypes.c_int * max(len(faces), 1))(*[int(v) for v in faces])
+    rc = lib.poisfft_plan_create(ctypes.byref(plan), dims, n_arr, L_arr, bc_arr, int(approx), int(dtype))
+    return rc, plan
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def solve(plan, phi, g, stream=None):
+    return lib.poisfft_solve(plan, _ptr(phi), _ptr(g), _stream(stream))
+
+
+def solve_host(plan, phi, g, stream=None):
+    return lib.poisfft_solve_host(plan, _ptr(phi), _ptr(g), _stream(stream))
+
+
+def check(plan, stream=None):
+    return lib.poisfft_check(plan, _stream(stream))
+
+
+def destroy(plan):
+    return lib.poisfft_destroy(plan)
+
+
+def plan_info(plan):
+    info = (ctypes.c_int64 * 4)()
+    rc = lib.poisfft_plan_info(plan, info)
+    return rc, list(info)
+
+
+class Plan:
+    """RAII wrapper: Plan(n, L, bc, approx, dtype); .solve(phi, g, stream)."""
+
+    def __init__(self, n, L, bc, approx=FD2, dtype=F32):
+        rc, p = plan_create(n, L, bc, approx, dtype)
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_plan_create")
+        self._p = p
+        self.n = tuple(int(v) for v in n)
+        self.dtype = dtype
+
+    @property
+    def handle(self):
+        return self._p
+
+    def solve(self, phi, g, stream=None):
+        rc = solve(self._p, phi, g, stream)
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_solve")
+
+    def solve_host(self, phi, g, stream=None):
+        rc = solve_host(self._p, phi, g, stream)
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_solve_host")
+
+    def check(self, stream=None):
+        return check(self._p, stream)
+
+    def info(self):
+        rc, info = plan_info(self._p)
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_plan_info")
+        return dict(launches=info[0], workspace_bytes=info[1], dominant_bytes=info[2], dominant_index=info[3])
+
+    def launches(self):
+        """Per launch position: dict(bytes, kernel, mode, axis)."""
+        out = []
+        for i in range(self.info()["launches"]):
+            v = (ctypes.c_int64 * 4)()
+            rc = lib.poisfft_launch_info(self._p, i, v)
+            if rc != OK:
+                raise PoisFFTError(rc, "poisfft_launch_info")
+            out.append(dict(bytes=v[0], kernel=("x_sweep", "strided_sweep")[v[1]],
+                            mode=("forward", "backward", "fused")[v[2]], axis="xyz"[v[3]]))
+        return out
+
+    def profile(self, enable=True):
+        rc = lib.poisfft_profile_enable(self._p, 1 if enable else 0)
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_profile_enable")
+
+    def profile_read(self):
+        """(summed ms per launch position, number of profiled solves)."""
+        cap = 16
+        ms = (ctypes.c_double * cap)()
+        nl, ns = ctypes.c_int(), ctypes.c_int()
+        rc = lib.poisfft_profile_read(self._p, ms, cap, ctypes.byref(nl), ctypes.byref(ns))
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_profile_read")
+        return [ms[i] for i in range(min(cap, nl.value))], ns.value
+
+    def close(self):
+        if self._p:
+            destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,480 @@
+// Device-side FFT engine for the sweep kernels (sm_103a).
+//
+// A CTA holds a tile of complex lines in shared memory and transforms every
+// line in place with mixed-radix decimation-in-frequency passes (natural
+// order in, digit-reversed order out; see dif_pass).  Radices 2, 3, 4, 5,
+// 7, 8, 16 and 32 are unrolled register butterflies; any other prime runs as
+// direct DFT butterflies through a scratch tile.
+//
+// The pre- and post-processing gathers turn the FFT into the real transforms
+// of Table 1 (see internal.h for the mapping of each kind).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace pf {
+
+// ---------------------------------------------------------------------------
+// complex arithmetic
+// ---------------------------------------------------------------------------
+template <typename T> struct CxOf;
+template <> struct CxOf<float> { using type = float2; };
+template <> struct CxOf<double> { using type = double2; };
+template <typename T> using cx = typename CxOf<T>::type;
+
+template <typename T> __device__ __forceinline__ cx<T> mkc(T r, T i) { cx<T> z; z.x = r; z.y = i; return z; }
+template <typename T> __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) { return mkc<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) { return mkc<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return mkc<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename T> __device__ __forceinline__ cx<T> cmulc(cx<T> a, cx<T> b) {
+  return mkc<T>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename T> __device__ __forceinline__ cx<T> cscale(cx<T> a, T s) { return mkc<T>(a.x * s, a.y * s); }
+template <typename T> __device__ __forceinline__ cx<T> cconj(cx<T> a) { return mkc<T>(a.x, -a.y); }
+template <typename T> __device__ __forceinline__ cx<T> mul_i(cx<T> a) { return mkc<T>(-a.y, a.x); }     // i*a
+template <typename T> __device__ __forceinline__ cx<T> mul_mi(cx<T> a) { return mkc<T>(a.y, -a.x); }    // -i*a
+template <typename T> __device__ __forceinline__ cx<T> czero() { return mkc<T>(T(0), T(0)); }
+
+// ---------------------------------------------------------------------------
+// unit-circle constants for the unrolled radices (correctly rounded decimals)
+// ---------------------------------------------------------------------------
+// cos(2 pi m / 32) for m = 0..8 (first quadrant)
+__host__ __device__ constexpr double q32(int m) {
+  return m == 0 ? 1.0 : m == 1 ? 0.9807852804032304 : m == 2 ? 0.9238795325112867
+       : m == 3 ? 0.8314696123025452 : m == 4 ? 0.7071067811865476 : m == 5 ? 0.5555702330196022
+       : m == 6 ? 0.3826834323650898 : m == 7 ? 0.19509032201612828 : 0.0;
+}
+__host__ __device__ constexpr int mod_pos(int a, int n) { return ((a % n) + n) % n; }
+// cos(2 pi m / 32), any m
+__host__ __device__ constexpr double cos32(int m) {
+  return mod_pos(m, 32) <= 8 ? q32(mod_pos(m, 32))
+       : mod_pos(m, 32) <= 16 ? -q32(16 - mod_pos(m, 32))
+       : mod_pos(m, 32) <= 24 ? -q32(mod_pos(m, 32) - 16)
+       : q32(32 - mod_pos(m, 32));
+}
+__host__ __device__ constexpr double sin32(int m) { return cos32(m - 8); }
+// cos / sin(2 pi m / N) for odd N in {3, 5, 7}
+__host__ __device__ constexpr double cos_odd(int N, int m) {
+  return N == 3 ? (mod_pos(m, 3) == 0 ? 1.0 : -0.5)
+       : N == 5 ? (mod_pos(m, 5) == 0 ? 1.0 : (mod_pos(m, 5) == 1 || mod_pos(m, 5) == 4) ? 0.30901699437494745 : -0.8090169943749475)
+       : (mod_pos(m, 7) == 0 ? 1.0 : (mod_pos(m, 7) == 1 || mod_pos(m, 7) == 6) ? 0.6234898018587335
+          : (mod_pos(m, 7) == 2 || mod_pos(m, 7) == 5) ? -0.2225209339563144 : -0.9009688679024191);
+}
+__host__ __device__ constexpr double sin_odd(int N, int m) {
+  return N == 3 ? (mod_pos(m, 3) == 0 ? 0.0 : mod_pos(m, 3) == 1 ? 0.8660254037844386 : -0.8660254037844386)
+       : N == 5 ? (mod_pos(m, 5) == 0 ? 0.0 : mod_pos(m, 5) == 1 ? 0.9510565162951535 : mod_pos(m, 5) == 2 ? 0.5877852522924731
+                   : mod_pos(m, 5) == 3 ? -0.5877852522924731 : -0.9510565162951535)
+       : (mod_pos(m, 7) == 0 ? 0.0 : mod_pos(m, 7) == 1 ? 0.7818314824680298 : mod_pos(m, 7) == 2 ? 0.9749279121818236
+          : mod_pos(m, 7) == 3 ? 0.4338837391175581 : mod_pos(m, 7) == 4 ? -0.4338837391175581
+          : mod_pos(m, 7) == 5 ? -0.9749279121818236 : -0.7818314824680298);
+}
+
+// a * exp(-+ 2 pi i m / N) for N dividing 32 (sign: forward '-', INV '+').
+// Called with compile-time m after unrolling, so the branches fold.
+template <typename T, int N, bool INV>
+__device__ __forceinline__ cx<T> tw_pow2(cx<T> a, int m) {
+  const int r = mod_pos(m, N);
+  if (r == 0) return a;
+  if (2 * r == N) return mkc<T>(-a.x, -a.y);
+  if (4 * r == N) return INV ? mul_i<T>(a) : mul_mi<T>(a);
+  if (4 * r == 3 * N) return INV ? mul_mi<T>(a) : mul_i<T>(a);
+  const T c = T(cos32(r * (32 / N)));
+  const T s = INV ? T(sin32(r * (32 / N))) : T(-sin32(r * (32 / N)));
+  return mkc<T>(a.x * c - a.y * s, a.x * s + a.y * c);
+}
+
+// ---------------------------------------------------------------------------
+// radix-R DFTs in registers (in place, natural order)
+// ---------------------------------------------------------------------------
+template <typename T, int R, bool INV> struct Dft;
+
+template <typename T, bool INV> struct Dft<T, 1, INV> {
+  static __device__ __forceinline__ void run(cx<T>*) {}
+};
+template <typename T, bool INV> struct Dft<T, 2, INV> {
+  static __device__ __forceinline__ void run(cx<T>* u) {
+    cx<T> a = cadd<T>(u[0], u[1]), b = csub<T>(u[0], u[1]);
+    u[0] = a; u[1] = b;
+  }
+};
+template <typename T, bool INV> struct Dft<T, 4, INV> {
+  static __device__ __forceinline__ void run(cx<T>* u) {
+    cx<T> s02 = cadd<T>(u[0], u[2]), d02 = csub<T>(u[0], u[2]);
+    cx<T> s13 = cadd<T>(u[1], u[3]), d13 = csub<T>(u[1], u[3]);
+    cx<T> r13 = INV ? mul_i<T>(d13) : mul_mi<T>(d13);
+    u[0] = cadd<T>(s02, s13);
+    u[2] = csub<T>(s02, s13);
+    u[1] = cadd<T>(d02, r13);
+    u[3] = csub<T>(d02, r13);
+  }
+};
+// odd prime radix: y_s = u0 + sum_q (u_q + u_{R-q}) cos(2 pi q s/R) -/+ i (u_q - u_{R-q}) sin(2 pi q s/R)
+template <typename T, int R, bool INV> struct DftOdd {
+  static __device__ __forceinline__ void run(cx<T>* u) {
+    constexpr int H = (R - 1) / 2;
+    cx<T> sp[H], sm[H];
+#pragma unroll
+    for (int q = 1; q <= H; q++) { sp[q - 1] = cadd<T>(u[q], u[R - q]); sm[q - 1] = csub<T>(u[q], u[R - q]); }
+    cx<T> y0 = u[0];
+#pragma unroll
+    for (int q = 0; q < H; q++) y0 = cadd<T>(y0, sp[q]);
+    cx<T> out[R];
+    out[0] = y0;
+#pragma unroll
+    for (int s = 1; s <= H; s++) {
+      cx<T> a = u[0], b = czero<T>();
+#pragma unroll
+      for (int q = 1; q <= H; q++) {
+        const T c = T(cos_odd(R, q * s)), sn = T(sin_odd(R, q * s));
+        a = mkc<T>(a.x + c * sp[q - 1].x, a.y + c * sp[q - 1].y);
+        b = mkc<T>(b.x + sn * sm[q - 1].x, b.y + sn * sm[q - 1].y);
+      }
+      // forward: y_s = a - i b, y_{R-s} = a + i b
+      cx<T> ib = mul_i<T>(b);
+      out[s] = INV ? cadd<T>(a, ib) : csub<T>(a, ib);
+      out[R - s] = INV ? csub<T>(a, ib) : cadd<T>(a, ib);
+    }
+#pragma unroll
+    for (int s = 0; s < R; s++) u[s] = out[s];
+  }
+};
+template <typename T, bool INV> struct Dft<T, 3, INV> : DftOdd<T, 3, INV> {};
+template <typename T, bool INV> struct Dft<T, 5, INV> : DftOdd<T, 5, INV> {};
+template <typename T, bool INV> struct Dft<T, 7, INV> : DftOdd<T, 7, INV> {};
+
+// N = A*B by one Cooley-Tukey step: input n = B*n1 + n2, output k = k1 + A*k2.
+template <typename T, int A, int B, bool INV>
+__device__ __forceinline__ void dft_ct(cx<T>* u) {
+  constexpr int N = A * B;
+  cx<T> t[N];
+#pragma unroll
+  for (int n2 = 0; n2 < B; n2++) {
+    cx<T> a[A];
+#pragma unroll
+    for (int n1 = 0; n1 < A; n1++) a[n1] = u[B * n1 + n2];
+    Dft<T, A, INV>::run(a);
+#pragma unroll
+    for (int k1 = 0; k1 < A; k1++) t[k1 * B + n2] = tw_pow2<T, N, INV>(a[k1], n2 * k1);
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < A; k1++) {
+    cx<T> b[B];
+#pragma unroll
+    for (int n2 = 0; n2 < B; n2++) b[n2] = t[k1 * B + n2];
+    Dft<T, B, INV>::run(b);
+#pragma unroll
+    for (int k2 = 0; k2 < B; k2++) u[k1 + A * k2] = b[k2];
+  }
+}
+template <typename T, bool INV> struct Dft<T, 8, INV> {
+  static __device__ __forceinline__ void run(cx<T>* u) { dft_ct<T, 2, 4, INV>(u); }
+};
+template <typename T, bool INV> struct Dft<T, 16, INV> {
+  static __device__ __forceinline__ void run(cx<T>* u) { dft_ct<T, 4, 4, INV>(u); }
+};
+template <typename T, bool INV> struct Dft<T, 32, INV> {
+  static __device__ __forceinline__ void run(cx<T>* u) { dft_ct<T, 4, 8, INV>(u); }
+};
+
+// ---------------------------------------------------------------------------
+// tile layouts
+// ---------------------------------------------------------------------------
+// Column tile of a strided sweep: element (m, c) at m*w + c (TMA box order).
+// Consecutive threads take consecutive columns, so every smem access of a
+// warp covers whole rows.
+struct ColTile {
+  int w, lw;
+  __device__ __forceinline__ int idx(int m, int c) const { return m * w + c; }
+  // split a flat index over (lines of length len) x (w columns)
+  __device__ __forceinline__ void split(int b, int /*len*/, int& i, int& c) const { c = b & (w - 1); i = b >> lw; }
+};
+// Row tile of the contiguous sweep: element (m, line) at line*ld + m.
+struct RowTile {
+  int ld;
+  __device__ __forceinline__ int idx(int m, int c) const { return c * ld + m; }
+  __device__ __forceinline__ void split(int b, int len, int& i, int& c) const { c = b / len; i = b - c * len; }
+};
+
+// ---------------------------------------------------------------------------
+// in-place decimation-in-frequency passes
+// ---------------------------------------------------------------------------
+// Pass i of radix R works on blocks of L = M/(R_1...R_{i-1}) points.  The
+// butterfly (block, j), j < L/R, reads the R points block*L + j + q*(L/R),
+// takes their radix-R DFT, multiplies output s by exp(-2 pi i j s / L) and
+// writes it back to block*L + j + s*(L/R).  Each butterfly owns its points,
+// so passes need one barrier each and no staging.  After the last pass the
+// DFT output k = s_1 + R_1 (s_2 + R_2 (s_3 + ...)) sits at position
+// sum_i s_i L_i/R_i (digit reversal); the post-processing gathers read it
+// through the `perm` table.
+template <typename T, int R, bool INV, class LAY>
+__device__ __noinline__ void dif_pass(cx<T>* __restrict__ buf, const LAY lay, int M, int ncol, int L,
+                                      const cx<T>* __restrict__ tw) {
+  const int Lr = L / R;
+  const int nbl = M / R;
+  const int nb = nbl * ncol;
+  for (int b = threadIdx.x; b < nb; b += kThreads) {
+    int t, c;
+    lay.split(b, nbl, t, c);
+    const int blk = t / Lr;
+    const int j = t - blk * Lr;
+    const int base = blk * L + j;
+    cx<T> u[R];
+#pragma unroll
+    for (int q = 0; q < R; q++) u[q] = buf[lay.idx(base + q * Lr, c)];
+    Dft<T, R, INV>::run(u);
+    if (j != 0) {
+#pragma unroll
+      for (int s = 1; s < R; s++) {
+        const cx<T> w = tw[(s - 1) * Lr + j];
+        u[s] = INV ? cmulc<T>(u[s], w) : cmul<T>(u[s], w);
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < R; s++) buf[lay.idx(base + s * Lr, c)] = u[s];
+  }
+  __syncthreads();
+}
+
+// Direct DFT butterflies for radices without an unrolled kernel (primes > 7):
+// every output reads its R inputs from `buf` and goes to `scratch`; the tile
+// is copied back afterwards.  O(R) work per point, no per-thread arrays.
+template <typename T, bool INV, class LAY>
+__device__ __noinline__ void dif_pass_generic(cx<T>* __restrict__ buf, cx<T>* __restrict__ scratch, const LAY lay,
+                                              int M, int ncol, int R, int L, const cx<T>* __restrict__ tw,
+                                              const cx<T>* __restrict__ roots) {
+  const int Lr = L / R;
+  const int total = M * ncol;
+  for (int e = threadIdx.x; e < total; e += kThreads) {
+    int pos, c;
+    lay.split(e, M, pos, c);
+    const int blk = pos / L;
+    const int rem = pos - blk * L;
+    const int s = rem / Lr;
+    const int j = rem - s * Lr;
+    const int base = blk * L + j;
+    cx<T> acc = czero<T>();
+    int qs = 0;  // (q*s) mod R
+    for (int q = 0; q < R; q++) {
+      const cx<T> r = roots[qs];
+      const cx<T> x = buf[lay.idx(base + q * Lr, c)];
+      acc = cadd<T>(acc, INV ? cmulc<T>(x, r) : cmul<T>(x, r));
+      qs += s;
+      if (qs >= R) qs -= R;
+    }
+    if (j != 0 && s != 0) {
+      const cx<T> w = tw[(s - 1) * Lr + j];
+      acc = INV ? cmulc<T>(acc, w) : cmul<T>(acc, w);
+    }
+    scratch[lay.idx(pos, c)] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < total; e += kThreads) {
+    int pos, c;
+    lay.split(e, M, pos, c);
+    buf[lay.idx(pos, c)] = scratch[lay.idx(pos, c)];
+  }
+  __syncthreads();
+}
+
+template <typename T, bool INV, int EMAX, class LAY>
+__device__ __forceinline__ void run_passes_dir(cx<T>* buf, cx<T>* scratch, const LAY lay, const FftDesc& f, int ncol,
+                                               const cx<T>* __restrict__ tables) {
+  for (int ps = 0; ps < f.npass; ps++) {
+    const int R = f.radix[ps];
+    const int L = f.p[ps];
+    const cx<T>* tw = tables + f.tw_off[ps];
+    switch (R) {
+      case 2: dif_pass<T, 2, INV>(buf, lay, f.M, ncol, L, tw); break;
+      case 3: dif_pass<T, 3, INV>(buf, lay, f.M, ncol, L, tw); break;
+      case 4: dif_pass<T, 4, INV>(buf, lay, f.M, ncol, L, tw); break;
+      case 5: dif_pass<T, 5, INV>(buf, lay, f.M, ncol, L, tw); break;
+      case 7: dif_pass<T, 7, INV>(buf, lay, f.M, ncol, L, tw); break;
+      case 8: dif_pass<T, 8, INV>(buf, lay, f.M, ncol, L, tw); break;
+      case 16: dif_pass<T, 16, INV>(buf, lay, f.M, ncol, L, tw); break;
+      case 32:
+        if constexpr (EMAX >= 32) { dif_pass<T, 32, INV>(buf, lay, f.M, ncol, L, tw); break; }
+        // fall through to the direct DFT when 32 complex values exceed the register budget
+      default:
+        dif_pass_generic<T, INV>(buf, scratch, lay, f.M, ncol, R, L, tw, tables + f.gen_off[ps]);
+        break;
+    }
+  }
+}
+
+template <typename T, int EMAX, class LAY>
+__device__ __forceinline__ void run_passes(cx<T>* buf, cx<T>* scratch, const LAY lay, const FftDesc& f, int ncol,
+                                           const cx<T>* tables, bool inverse) {
+  if (inverse)
+    run_passes_dir<T, true, EMAX>(buf, scratch, lay, f, ncol, tables);
+  else
+    run_passes_dir<T, false, EMAX>(buf, scratch, lay, f, ncol, tables);
+}
+
+// ---------------------------------------------------------------------------
+// pre- and post-processing gathers (Table 1 transforms from one FFT)
+// ---------------------------------------------------------------------------
+// FFT input position m of the transform `kind` applied to the source line
+// held in rows 0..n-1 of `buf` (column c).  mk[k] = exp(-i pi k/(2n)).
+template <typename T, class LAY>
+__device__ __forceinline__ cx<T> pre_value(const cx<T>* buf, const LAY& lay, int kind, int n, int M, int m, int c,
+                                           const cx<T>* __restrict__ mk) {
+  switch (kind) {
+    case TK_DCT2:
+    case TK_DST2: {
+      // v_m = x_{2m} (m < ceil(n/2)), v_m = x_{2n-1-2m} otherwise
+      const int src = (2 * m < n) ? 2 * m : 2 * n - 1 - 2 * m;
+      cx<T> v = buf[lay.idx(src, c)];
+      if (kind == TK_DST2 && (src & 1)) v = mkc<T>(-v.x, -v.y);  // DST-II(x)_k = DCT-II((-1)^j x_j)_{n-1-k}
+      return v;
+    }
+    case TK_DST1: {  // odd extension of length 2(n+1)
+      if (m == 0 || m == n + 1) return czero<T>();
+      if (m <= n) return buf[lay.idx(m - 1, c)];
+      const cx<T> v = buf[lay.idx(M - 1 - m, c)];
+      return mkc<T>(-v.x, -v.y);
+    }
+    case TK_DCT1:  // even extension of length 2(n-1)
+      return buf[lay.idx(m < n ? m : M - m, c)];
+    case TK_DCT3:
+    case TK_DST3: {
+      // DCT-III: V_m = conj(w_m) (f_m - i f_{n-m}), f_n = 0
+      // DST-III(f)_k = (-1)^k DCT-III(h)_k with h_j = f_{n-1-j}
+      cx<T> a, b;
+      if (kind == TK_DCT3) {
+        a = buf[lay.idx(m, c)];
+        b = (m == 0) ? czero<T>() : buf[lay.idx(n - m, c)];
+      } else {
+        a = buf[lay.idx(n - 1 - m, c)];
+        b = (m == 0) ? czero<T>() : buf[lay.idx(m - 1, c)];
+      }
+      const cx<T> t = mkc<T>(a.x + b.y, a.y - b.x);  // a - i b
+      return cmulc<T>(t, mk[m]);
+    }
+    default:
+      return buf[lay.idx(m, c)];
+  }
+}
+
+// Output k of the transform `kind` from the FFT output held in `buf`; FFT
+// output index i sits at position perm[i] (digit reversal of the passes).
+template <typename T, class LAY>
+__device__ __forceinline__ cx<T> post_value(const cx<T>* buf, const LAY& lay, int kind, int n, int k, int c,
+                                            const cx<T>* __restrict__ mk, const int* __restrict__ perm) {
+  switch (kind) {
+    case TK_DCT2:
+    case TK_DST2: {
+      // X_k = w_k Y_k + conj(w_k) Y_{(n-k) mod n};  DST-II reads DCT-II output n-1-k
+      const int kk = (kind == TK_DCT2) ? k : n - 1 - k;
+      const cx<T> w = mk[kk];
+      const cx<T> y1 = buf[lay.idx(perm[kk], c)];
+      const cx<T> y2 = buf[lay.idx(perm[kk == 0 ? 0 : n - kk], c)];
+      return cadd<T>(cmul<T>(w, y1), cmulc<T>(y2, w));
+    }
+    case TK_DST1:
+      return mul_i<T>(buf[lay.idx(perm[k + 1], c)]);
+    case TK_DCT3:
+    case TK_DST3: {
+      // outputs 2j and 2j+1 are FFT outputs j and n-1-j
+      const int pos = (k & 1) ? n - 1 - (k >> 1) : (k >> 1);
+      cx<T> v = buf[lay.idx(perm[pos], c)];
+      if (kind == TK_DST3 && (k & 1)) v = mkc<T>(-v.x, -v.y);
+      return v;
+    }
+    default:  // DFT, IDFT, DCT1, NULL
+      return buf[lay.idx(perm[k], c)];
+  }
+}
+
+inline __device__ bool kind_needs_pre(int kind) {
+  return !(kind == TK_DFT || kind == TK_IDFT || kind == TK_NULL);
+}
+
+// In-place pre-processing of a whole tile: rows 0..n-1 (source) -> 0..M-1.
+template <typename T, int EMAX, class LAY>
+__device__ __forceinline__ void pre_tile(cx<T>* buf, const LAY lay, int kind, int n, int M, int ncol,
+                                         const cx<T>* __restrict__ mk) {
+  if (!kind_needs_pre(kind)) return;
+  cx<T> v[EMAX];
+  const int total = M * ncol;
+#pragma unroll
+  for (int j = 0; j < EMAX; j++) {
+    const int e = threadIdx.x + j * kThreads;
+    if (e < total) {
+      int m, c;
+      lay.split(e, M, m, c);
+      v[j] = pre_value<T>(buf, lay, kind, n, M, m, c, mk);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < EMAX; j++) {
+    const int e = threadIdx.x + j * kThreads;
+    if (e < total) {
+      int m, c;
+      lay.split(e, M, m, c);
+      buf[lay.idx(m, c)] = v[j];
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier / TMA (cp.async.bulk.tensor) wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for phase `parity` of the barrier for at most ~2 s of wall time.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t it = 0; it < (1u << 30); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u && globaltimer_ns() - t0 > 2000000000ull) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+}  // namespace pf

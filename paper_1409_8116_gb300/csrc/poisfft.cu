@@ -1,0 +1,685 @@
+// Planner and C interface of the GB300 Poisson solver (see include/poisfft.h).
+//
+// The planner picks, per axis, the Table 2 transform pair of the axis's
+// boundary condition, the FFT length and its radix passes, builds the FP64
+// twiddle and eigenvalue tables (Tables 3 and 4) with exactly reduced angles
+// and rounds them once to the solve precision, sizes the tiles of every
+// sweep kernel, encodes the TMA tensor maps of the workspace and allocates
+// it.  A solve enqueues the sweeps (Sec. 2.1 steps 1-3, Sec. 2.3 order):
+//   3D: x forward, y forward, z forward+divide+backward, y backward, x backward
+//   2D: x forward, y forward+divide+backward, x backward
+//   1D: x forward, divide (length-1 axis), x backward
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "../../include/poisfft.h"
+#include "internal.h"
+#include "launch.h"
+
+using namespace pf;
+
+
+namespace {
+
+constexpr size_t kSmemLimit = 200 * 1024;   // dynamic smem budget of one CTA
+constexpr size_t kSmemTarget = 64 * 1024;   // preferred tile size (several CTAs per SM)
+
+// ---------------------------------------------------------------------------
+// FP64 trigonometry with exactly reduced arguments: angle 2 pi m / N
+// ---------------------------------------------------------------------------
+void sincos_2pi_frac(long long m, long long N, double* s, double* c) {
+  long long r = m % N;
+  if (r < 0) r += N;
+  const long long q = (4 * r) / N;       // quadrant
+  long long rem = 4 * r - q * N;         // angle = q pi/2 + (pi/2) rem/N
+  bool swap = false;
+  if (2 * rem > N) { rem = N - rem; swap = true; }
+  const double phi = (M_PI / 2.0) * (double)rem / (double)N;
+  double s1 = sin(phi), c1 = cos(phi);
+  if (swap) { const double t = s1; s1 = c1; c1 = t; }
+  switch (q) {
+    case 0: *c = c1; *s = s1; break;
+    case 1: *c = -s1; *s = c1; break;
+    case 2: *c = -c1; *s = -s1; break;
+    default: *c = s1; *s = -c1; break;
+  }
+}
+
+double sin_pi_frac(long long num, long long den) {  // sin(pi num/den)
+  double s, c;
+  sincos_2pi_frac(num, 2 * den, &s, &c);
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// per-axis transform description
+// ---------------------------------------------------------------------------
+bool is_unrolled_radix(int r, int emax) {
+  return r == 2 || r == 3 || r == 4 || r == 5 || r == 7 || r == 8 || r == 16 || (r == 32 && emax >= 32);
+}
+
+// Factor M into DIF passes: powers of two grouped into balanced radices
+// up to 32 (16 for FP64), then 3, 5, 7, then any other prime (direct DFT).
+void factor_passes(int M, int emax, std::vector<int>& radices) {
+  radices.clear();
+  int e2 = 0;
+  while (M % 2 == 0) { M /= 2; e2++; }
+  const int maxlog = emax >= 32 ? 5 : 4;
+  if (e2 > 0) {
+    const int np = (e2 + maxlog - 1) / maxlog;
+    for (int i = 0; i < np; i++) {
+      const int take = e2 / np + (i < e2 % np ? 1 : 0);
+      radices.push_back(1 << take);
+    }
+  }
+  for (int p : {3, 5, 7}) while (M % p == 0) { radices.push_back(p); M /= p; }
+  for (int p = 11; (long long)p * p <= M; p += 2)
+    while (M % p == 0) { radices.push_back(p); M /= p; }
+  if (M > 1) radices.push_back(M);
+}
+
+struct AxisPlan {
+  int bc = POISFFT_P;
+  int n = 1;
+  double L = 1.0;
+  AxisDesc d{};
+  std::vector<double> tab_re, tab_im;   // complex table in FP64
+  std::vector<double> lam;              // eigenvalues, FP64
+  std::vector<int> perm;                // FFT output index -> position after the DIF passes
+  double scale = 1.0;                   // Table 2 normalisation of the axis
+  int max_ncol = 0;                     // max lines / columns per CTA from the register budget
+  bool generic = false;                 // a direct-DFT pass needs a scratch tile
+};
+
+int build_axis(AxisPlan& ax, int bc, int n, double L, int approx, int emax, bool null_axis) {
+  ax.bc = bc;
+  ax.n = n;
+  ax.L = L;
+  AxisDesc& d = ax.d;
+  memset(&d, 0, sizeof(d));
+  d.n = n;
+  d.mk_off = -1;
+  int M = n;
+  if (null_axis) {
+    d.kfwd = d.kinv = TK_NULL;
+    M = 1;
+    ax.scale = 1.0;
+  } else {
+    switch (bc) {
+      case POISFFT_P: d.kfwd = TK_DFT; d.kinv = TK_IDFT; M = n; ax.scale = 1.0 / n; break;
+      case POISFFT_DR: d.kfwd = d.kinv = TK_DST1; M = 2 * (n + 1); ax.scale = 1.0 / (2.0 * (n + 1)); break;
+      case POISFFT_DS: d.kfwd = TK_DST2; d.kinv = TK_DST3; M = n; ax.scale = 1.0 / (2.0 * n); break;
+      case POISFFT_NR: d.kfwd = d.kinv = TK_DCT1; M = 2 * (n - 1); ax.scale = 1.0 / (2.0 * (n - 1)); break;
+      case POISFFT_NS: d.kfwd = TK_DCT2; d.kinv = TK_DCT3; M = n; ax.scale = 1.0 / (2.0 * n); break;
+      default: return POISFFT_ERR_INVALID_ARG;
+    }
+  }
+  d.fft.M = M;
+  std::vector<int> radices;
+  factor_passes(M, emax, radices);
+  if ((int)radices.size() > kMaxPass) return POISFFT_ERR_UNSUPPORTED_SIZE;
+  d.fft.npass = (int)radices.size();
+  ax.tab_re.clear();
+  ax.tab_im.clear();
+  ax.generic = false;
+  auto push = [&](double re, double im) { ax.tab_re.push_back(re); ax.tab_im.push_back(im); };
+  // register budget: the pre/post gathers stage EMAX elements per thread
+  const long long cap = (long long)kThreads * emax / M;
+  int Lb = M;  // block length of the pass
+  for (int i = 0; i < d.fft.npass; i++) {
+    const int R = radices[i];
+    d.fft.radix[i] = R;
+    d.fft.p[i] = Lb;
+    d.fft.tw_off[i] = (int)ax.tab_re.size();
+    const int Lr = Lb / R;
+    for (int s = 1; s < R; s++)
+      for (int j = 0; j < Lr; j++) {
+        double sn, c;
+        sincos_2pi_frac((long long)j * s, Lb, &sn, &c);  // exp(-2 pi i j s / Lb)
+        push(c, -sn);
+      }
+    if (is_unrolled_radix(R, emax)) {
+      d.fft.gen_off[i] = -1;
+    } else {
+      ax.generic = true;
+      d.fft.gen_off[i] = (int)ax.tab_re.size();
+      for (int m = 0; m < R; m++) {
+        double sn, c;
+        sincos_2pi_frac(m, R, &sn, &c);
+        push(c, -sn);
+      }
+    }
+    Lb = Lr;
+  }
+  // digit reversal: FFT output k = s_1 + R_1 (s_2 + R_2 (...)) sits at sum_i s_i L_i / R_i
+  ax.perm.assign(M, 0);
+  for (int k = 0; k < M; k++) {
+    int rem = k, pos = 0, Li = M;
+    for (int i = 0; i < d.fft.npass; i++) {
+      const int R = d.fft.radix[i];
+      pos += (rem % R) * (Li / R);
+      rem /= R;
+      Li /= R;
+    }
+    ax.perm[k] = pos;
+  }
+  if (d.kfwd == TK_DCT2 || d.kfwd == TK_DST2) {
+    d.mk_off = (int)ax.tab_re.size();
+    for (int k = 0; k < n; k++) {
+      double s, c;
+      sincos_2pi_frac(k, 4LL * n, &s, &c);  // exp(-i pi k/(2n))
+      push(c, -s);
+    }
+  }
+  if (ax.tab_re.empty()) push(1.0, 0.0);
+  ax.max_ncol = (int)std::max<long long>(cap, 0);
+
+  // eigenvalues (Table 3 / Table 4)
+  ax.lam.assign(n, 0.0);
+  if (!null_axis) {
+    for (int k = 0; k < n; k++) {
+      double lam = 0.0;
+      if (approx == POISFFT_SPECTRAL) {
+        switch (bc) {
+          case POISFFT_P: { const int m = std::min(k, n - k); lam = -pow(2.0 * M_PI * m / L, 2); break; }
+          case POISFFT_DR:
+          case POISFFT_DS: lam = -pow(M_PI * (k + 1) / L, 2); break;
+          default: lam = -pow(M_PI * k / L, 2); break;
+        }
+      } else {
+        double dx, s;
+        switch (bc) {
+          case POISFFT_P: dx = L / n; s = sin_pi_frac(k, n); break;
+          case POISFFT_DR: dx = L / (n + 1); s = sin_pi_frac(k + 1, 2LL * (n + 1)); break;
+          case POISFFT_DS: dx = L / n; s = sin_pi_frac(k + 1, 2LL * n); break;
+          case POISFFT_NR: dx = L / (n - 1); s = sin_pi_frac(k, 2LL * (n - 1)); break;
+          default: dx = L / n; s = sin_pi_frac(k, 2LL * n); break;
+        }
+        lam = -(2.0 * s / dx) * (2.0 * s / dx);
+      }
+      ax.lam[k] = lam;
+    }
+  }
+  return POISFFT_OK;
+}
+
+struct SweepLaunch {
+  int kind;               // 0 x sweep, 1 strided sweep
+  XArgs xa;
+  StridedArgs sa;
+  int map;                // tensor map index (strided)
+  unsigned grid;
+  size_t smem;
+  long long bytes;        // algorithmic HBM bytes (read + write)
+};
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+int pow2_floor(long long v) {
+  int p = 1;
+  while ((long long)p * 2 <= v) p *= 2;
+  return p;
+}
+int pow2_ceil(long long v) {
+  int p = 1;
+  while (p < v) p *= 2;
+  return p;
+}
+int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) l++;
+  return l;
+}
+
+}  // namespace
+
+struct poisfft_plan {
+  int dims = 0;
+  int dtype = POISFFT_F32;
+  int approx = POISFFT_FD2;
+  int nx = 1, ny = 1, nz = 1;
+  size_t esize = 4;              // bytes of one real element
+  int r2c = 0;
+  int ncols = 0, pitch = 0;      // workspace complex columns (valid) and pitch
+  int singular = 0;
+  AxisPlan axes[3];              // x, y, z (missing axes are length-1 null axes)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  void* tables[3] = {nullptr, nullptr, nullptr};
+  void* lam[3] = {nullptr, nullptr, nullptr};
+  int* perm[3] = {nullptr, nullptr, nullptr};
+  int* err = nullptr;
+  CUtensorMap maps[2];
+  std::vector<SweepLaunch> sweeps;
+  void* stage_g = nullptr;
+  void* stage_phi = nullptr;
+  size_t field_bytes = 0;
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;   // (launches + 1) per profiled solve
+};
+
+namespace {
+
+void free_plan(poisfft_plan* p) {
+  if (!p) return;
+  if (p->ws) cudaFree(p->ws);
+  for (int i = 0; i < 3; i++) {
+    if (p->tables[i]) cudaFree(p->tables[i]);
+    if (p->lam[i]) cudaFree(p->lam[i]);
+    if (p->perm[i]) cudaFree(p->perm[i]);
+  }
+  if (p->err) cudaFree(p->err);
+  if (p->stage_g) cudaFree(p->stage_g);
+  if (p->stage_phi) cudaFree(p->stage_phi);
+  for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+  delete p;
+}
+
+template <typename T>
+int upload_tables(poisfft_plan* p) {
+  for (int a = 0; a < 3; a++) {
+    AxisPlan& ax = p->axes[a];
+    const size_t nt = ax.tab_re.size();
+    std::vector<T> tab(2 * nt);
+    for (size_t i = 0; i < nt; i++) { tab[2 * i] = (T)ax.tab_re[i]; tab[2 * i + 1] = (T)ax.tab_im[i]; }
+    std::vector<T> lam(ax.lam.size());
+    for (size_t i = 0; i < lam.size(); i++) lam[i] = (T)ax.lam[i];
+    if (cudaMalloc(&p->tables[a], tab.size() * sizeof(T)) != cudaSuccess) return POISFFT_ERR_ALLOC;
+    if (cudaMalloc(&p->lam[a], std::max<size_t>(lam.size(), 1) * sizeof(T)) != cudaSuccess) return POISFFT_ERR_ALLOC;
+    if (cudaMemcpy(p->tables[a], tab.data(), tab.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+      return POISFFT_ERR_CUDA;
+    if (cudaMemcpy(p->lam[a], lam.data(), lam.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+      return POISFFT_ERR_CUDA;
+    if (cudaMalloc(&p->perm[a], ax.perm.size() * sizeof(int)) != cudaSuccess) return POISFFT_ERR_ALLOC;
+    if (cudaMemcpy(p->perm[a], ax.perm.data(), ax.perm.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+      return POISFFT_ERR_CUDA;
+  }
+  return POISFFT_OK;
+}
+
+// x sweep configuration
+int plan_x_sweep(poisfft_plan* p, int mode, SweepLaunch& L) {
+  AxisPlan& ax = p->axes[0];
+  const int M = ax.d.fft.M;
+  const size_t cx = 2 * p->esize;
+  const long long nrows = (long long)p->ny * p->nz;
+  const long long pairs = (nrows + 1) / 2;
+  long long lines = ax.max_ncol;
+  const size_t per_line = (size_t)M * cx * (ax.generic ? 2 : 1);
+  lines = std::min<long long>(lines, (long long)(kSmemTarget / per_line));
+  lines = std::min<long long>(lines, pairs);
+  if (lines < 1) {
+    if (ax.max_ncol >= 1 && per_line <= kSmemLimit) lines = 1;
+    else return POISFFT_ERR_UNSUPPORTED_SIZE;
+  }
+  memset(&L, 0, sizeof(L));
+  L.kind = 0;
+  XArgs& a = L.xa;
+  a.ax = ax.d;
+  a.tables = p->tables[0];
+  a.mode = mode;
+  a.r2c = p->r2c;
+  a.nx = p->nx;
+  a.lines = (int)lines;
+  a.ld = M;
+  a.nrows = nrows;
+  a.ws_ld = p->r2c ? p->pitch : 2LL * p->pitch;
+  a.ws = p->ws;
+  a.err = p->err;
+  L.grid = (unsigned)((pairs + lines - 1) / lines);
+  L.smem = (size_t)lines * per_line;
+  const long long field = nrows * p->nx * (long long)p->esize;
+  const long long wsb = nrows * (long long)p->ncols * (long long)cx;
+  L.bytes = field + (p->r2c ? wsb : field);
+  return POISFFT_OK;
+}
+
+// strided sweep along axis `a` (1 = y, 2 = z)
+int plan_strided_sweep(poisfft_plan* p, int axis, int mode, SweepLaunch& L) {
+  AxisPlan& ax = p->axes[axis];
+  const int M = ax.d.fft.M;
+  const int n = ax.n;
+  const size_t cx = 2 * p->esize;
+  const int wmin = p->esize == 4 ? 2 : 1;
+  int nbox, box_h;
+  if (n <= 256) { nbox = 1; box_h = n; }
+  else {
+    nbox = (n + 255) / 256;
+    box_h = (n + nbox - 1) / nbox;
+    box_h = (box_h + 15) / 16 * 16;
+  }
+  const int rows_alloc = std::max(M, nbox * box_h);
+  const size_t per_col = (size_t)rows_alloc * cx * (ax.generic ? 2 : 1);
+  long long w = std::min<long long>(ax.max_ncol, 128);
+  w = std::min<long long>(w, pow2_ceil(p->ncols));
+  w = std::min<long long>(w, (long long)(kSmemTarget / per_col));
+  w = pow2_floor(std::max<long long>(w, 1));
+  if (w < wmin) w = wmin;
+  if (w > ax.max_ncol || (size_t)w * per_col + 16 > kSmemLimit) return POISFFT_ERR_UNSUPPORTED_SIZE;
+  memset(&L, 0, sizeof(L));
+  L.kind = 1;
+  L.map = axis - 1;
+  StridedArgs& s = L.sa;
+  s.ax = ax.d;
+  s.tables = p->tables[axis];
+  s.mode = mode;
+  s.axis_dim = axis;
+  s.w = (int)w;
+  s.lw = ilog2((int)w);
+  s.ncols = p->ncols;
+  s.ntile_c = (p->ncols + (int)w - 1) / (int)w;
+  s.nouter = axis == 1 ? p->nz : p->ny;
+  s.box_h = box_h;
+  s.nbox = nbox;
+  s.rows_alloc = rows_alloc;
+  s.bar_off = (int)(((size_t)w * per_col + 15) / 16 * 16);
+  s.s_axis = axis == 1 ? (long long)p->pitch : (long long)p->pitch * p->ny;
+  s.s_outer = axis == 1 ? (long long)p->pitch * p->ny : (long long)p->pitch;
+  s.data = p->ws;
+  s.lam_in = p->lam[0];
+  s.lam_ax = p->lam[axis];
+  s.lam_out = p->lam[axis == 1 ? 2 : 1];
+  double sc = 1.0;
+  for (int i = 0; i < 3; i++) sc *= p->axes[i].scale;
+  s.scale = sc;
+  s.singular = p->singular;
+  s.packed = p->r2c ? 0 : 1;
+  s.nx = p->nx;
+  s.err = p->err;
+  L.grid = (unsigned)((long long)s.ntile_c * s.nouter);
+  L.smem = (size_t)s.bar_off + 16;
+  L.bytes = 2LL * p->ncols * (long long)p->ny * p->nz * (long long)cx;
+  return POISFFT_OK;
+}
+
+int encode_maps(poisfft_plan* p) {
+  EncodeTiledFn enc = get_encode_fn();
+  if (!enc) return POISFFT_ERR_CUDA;
+  const CUtensorMapDataType dt = p->esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  const cuuint64_t gdim[3] = {(cuuint64_t)2 * p->ncols, (cuuint64_t)p->ny, (cuuint64_t)p->nz};
+  const cuuint64_t row = (cuuint64_t)p->pitch * 2 * p->esize;
+  const cuuint64_t gstride[2] = {row, row * (cuuint64_t)p->ny};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  for (auto& L : p->sweeps) {
+    if (L.kind != 1) continue;
+    const StridedArgs& s = L.sa;
+    cuuint32_t box[3];
+    box[0] = (cuuint32_t)(2 * s.w);
+    box[1] = s.axis_dim == 1 ? (cuuint32_t)s.box_h : 1u;
+    box[2] = s.axis_dim == 2 ? (cuuint32_t)s.box_h : 1u;
+    CUresult r = enc(&p->maps[L.map], dt, 3, p->ws, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return POISFFT_ERR_CUDA;
+  }
+  return POISFFT_OK;
+}
+
+int record_event(poisfft_plan* p, cudaStream_t st) {
+  cudaEvent_t ev;
+  if (cudaEventCreate(&ev) != cudaSuccess) return POISFFT_ERR_CUDA;
+  p->events.push_back(ev);
+  return cudaEventRecord(ev, st) == cudaSuccess ? POISFFT_OK : POISFFT_ERR_CUDA;
+}
+
+template <typename T>
+int enqueue(poisfft_plan* p, void* phi, const void* g, cudaStream_t st) {
+  for (auto& L : p->sweeps) {
+    if (p->profiling && record_event(p, st) != POISFFT_OK) return POISFFT_ERR_CUDA;
+    cudaError_t e;
+    if (L.kind == 0) {
+      XArgs a = L.xa;
+      a.g = g;
+      a.phi = phi;
+      e = launch_x_sweep<T>(a, L.grid, L.smem, st);
+    } else {
+      e = launch_strided_sweep<T>(p->maps[L.map], L.sa, L.grid, L.smem, st);
+    }
+    if (e != cudaSuccess) return POISFFT_ERR_CUDA;
+  }
+  if (p->profiling && record_event(p, st) != POISFFT_OK) return POISFFT_ERR_CUDA;
+  return POISFFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* poisfft_status_string(int status) {
+  switch (status) {
+    case POISFFT_OK: return "ok";
+    case POISFFT_ERR_INVALID_ARG: return "invalid argument";
+    case POISFFT_ERR_UNSUPPORTED_BC: return "unsupported boundary-condition combination";
+    case POISFFT_ERR_UNSUPPORTED_SIZE: return "unsupported grid size";
+    case POISFFT_ERR_ALLOC: return "allocation failed";
+    case POISFFT_ERR_CUDA: return "CUDA error";
+    case POISFFT_ERR_MISALIGNED: return "misaligned pointer";
+    case POISFFT_ERR_TIMEOUT: return "device wait timed out";
+    case POISFFT_ERR_NOT_IMPLEMENTED: return "not implemented";
+    default: return "unknown status";
+  }
+}
+
+int poisfft_plan_create(poisfft_plan** out, int dims, const int64_t n[], const double L[], const int bc[],
+                        int approx, int dtype) {
+  if (!out) return POISFFT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!n || !L || !bc || dims < 1 || dims > 3) return POISFFT_ERR_INVALID_ARG;
+  if (approx != POISFFT_SPECTRAL && approx != POISFFT_FD2) return POISFFT_ERR_INVALID_ARG;
+  if (dtype != POISFFT_F32 && dtype != POISFFT_F64) return POISFFT_ERR_INVALID_ARG;
+  int bca[3] = {POISFFT_P, POISFFT_P, POISFFT_P};
+  long long nn[3] = {1, 1, 1};
+  double LL[3] = {1.0, 1.0, 1.0};
+  for (int a = 0; a < dims; a++) {
+    if (n[a] < 1 || n[a] > (1 << 24)) return POISFFT_ERR_INVALID_ARG;
+    if (!(L[a] > 0.0) || !isfinite(L[a])) return POISFFT_ERR_INVALID_ARG;
+    const int b0 = bc[2 * a], b1 = bc[2 * a + 1];
+    if (b0 < POISFFT_P || b0 > POISFFT_NS || b1 < POISFFT_P || b1 > POISFFT_NS) return POISFFT_ERR_INVALID_ARG;
+    if (b0 != b1) return POISFFT_ERR_UNSUPPORTED_BC;
+    if (b0 == POISFFT_NR && n[a] < 2) return POISFFT_ERR_INVALID_ARG;
+    bca[a] = b0;
+    nn[a] = n[a];
+    LL[a] = L[a];
+  }
+  if ((double)nn[0] * nn[1] * nn[2] > 4.0e10) return POISFFT_ERR_UNSUPPORTED_SIZE;
+  // x periodic -> half-spectrum workspace; no periodic axis -> real workspace.
+  // x non-periodic with a periodic y or z is a valid problem outside this build.
+  const bool xper = bca[0] == POISFFT_P;
+  bool any_per_yz = false;
+  for (int a = 1; a < dims; a++) any_per_yz |= bca[a] == POISFFT_P;
+  if (!xper && any_per_yz) return POISFFT_ERR_NOT_IMPLEMENTED;
+
+  poisfft_plan* p = new (std::nothrow) poisfft_plan();
+  if (!p) return POISFFT_ERR_ALLOC;
+  p->dims = dims;
+  p->dtype = dtype;
+  p->approx = approx;
+  p->nx = (int)nn[0];
+  p->ny = (int)nn[1];
+  p->nz = (int)nn[2];
+  p->esize = dtype == POISFFT_F32 ? 4 : 8;
+  p->r2c = xper ? 1 : 0;
+  const int emax = dtype == POISFFT_F32 ? 32 : 16;
+  bool sing = true;
+  for (int a = 0; a < 3; a++) {
+    const bool null_axis = a >= dims;
+    int rc = build_axis(p->axes[a], bca[a], (int)nn[a], LL[a], approx, emax, null_axis);
+    if (rc != POISFFT_OK) { free_plan(p); return rc; }
+    if (!null_axis) sing = sing && (bca[a] == POISFFT_P || bca[a] == POISFFT_NR || bca[a] == POISFFT_NS);
+  }
+  p->singular = sing ? 1 : 0;
+  p->ncols = p->r2c ? p->nx / 2 + 1 : (p->nx + 1) / 2;
+  p->pitch = (p->ncols + 1) / 2 * 2;
+  p->field_bytes = (size_t)p->nx * p->ny * p->nz * p->esize;
+  p->ws_bytes = (size_t)p->pitch * 2 * p->esize * p->ny * p->nz;
+
+  // sweep sequence and tiling (host only, before any CUDA call)
+  std::vector<SweepLaunch> sw;
+  SweepLaunch Ls;
+  int rc;
+  if ((rc = plan_x_sweep(p, 0, Ls)) != POISFFT_OK) { free_plan(p); return rc; }
+  sw.push_back(Ls);
+  const int fused_axis = dims == 3 ? 2 : 1;
+  if (dims == 3) {
+    if ((rc = plan_strided_sweep(p, 1, 0, Ls)) != POISFFT_OK) { free_plan(p); return rc; }
+    sw.push_back(Ls);
+  }
+  if ((rc = plan_strided_sweep(p, fused_axis, 2, Ls)) != POISFFT_OK) { free_plan(p); return rc; }
+  sw.push_back(Ls);
+  if (dims == 3) {
+    if ((rc = plan_strided_sweep(p, 1, 1, Ls)) != POISFFT_OK) { free_plan(p); return rc; }
+    sw.push_back(Ls);
+  }
+  if ((rc = plan_x_sweep(p, 1, Ls)) != POISFFT_OK) { free_plan(p); return rc; }
+  sw.push_back(Ls);
+  p->sweeps = sw;
+
+  // device resources
+  if (cudaMalloc(&p->err, sizeof(int)) != cudaSuccess) { cudaGetLastError(); free_plan(p); return POISFFT_ERR_CUDA; }
+  if (cudaMemset(p->err, 0, sizeof(int)) != cudaSuccess) { free_plan(p); return POISFFT_ERR_CUDA; }
+  if (cudaMalloc(&p->ws, p->ws_bytes) != cudaSuccess) { cudaGetLastError(); free_plan(p); return POISFFT_ERR_ALLOC; }
+  if (cudaMemset(p->ws, 0, p->ws_bytes) != cudaSuccess) { free_plan(p); return POISFFT_ERR_CUDA; }
+  rc = p->esize == 4 ? upload_tables<float>(p) : upload_tables<double>(p);
+  if (rc != POISFFT_OK) { cudaGetLastError(); free_plan(p); return rc; }
+  // the sweeps were planned before the buffers existed: patch the pointers
+  for (auto& L : p->sweeps) {
+    if (L.kind == 0) {
+      L.xa.tables = p->tables[0];
+      L.xa.perm = p->perm[0];
+      L.xa.ws = p->ws;
+      L.xa.err = p->err;
+    } else {
+      const int a = L.sa.axis_dim;
+      L.sa.tables = p->tables[a];
+      L.sa.perm = p->perm[a];
+      L.sa.data = p->ws;
+      L.sa.lam_in = p->lam[0];
+      L.sa.lam_ax = p->lam[a];
+      L.sa.lam_out = p->lam[a == 1 ? 2 : 1];
+      L.sa.err = p->err;
+    }
+  }
+  if ((rc = encode_maps(p)) != POISFFT_OK) { free_plan(p); return rc; }
+  *out = p;
+  return POISFFT_OK;
+}
+
+int poisfft_solve(poisfft_plan* p, void* phi, const void* g, void* stream) {
+  if (!p || !phi || !g) return POISFFT_ERR_INVALID_ARG;
+  if (((uintptr_t)phi % p->esize) != 0 || ((uintptr_t)g % p->esize) != 0) return POISFFT_ERR_MISALIGNED;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  return p->esize == 4 ? enqueue<float>(p, phi, g, st) : enqueue<double>(p, phi, g, st);
+}
+
+int poisfft_solve_host(poisfft_plan* p, void* phi_host, const void* g_host, void* stream) {
+  if (!p || !phi_host || !g_host) return POISFFT_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (!p->stage_g) {
+    if (cudaMalloc(&p->stage_g, p->field_bytes) != cudaSuccess) { cudaGetLastError(); p->stage_g = nullptr; return POISFFT_ERR_ALLOC; }
+  }
+  if (!p->stage_phi) {
+    if (cudaMalloc(&p->stage_phi, p->field_bytes) != cudaSuccess) { cudaGetLastError(); p->stage_phi = nullptr; return POISFFT_ERR_ALLOC; }
+  }
+  if (cudaMemcpyAsync(p->stage_g, g_host, p->field_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return POISFFT_ERR_CUDA;
+  int rc = poisfft_solve(p, p->stage_phi, p->stage_g, stream);
+  if (rc != POISFFT_OK) return rc;
+  if (cudaMemcpyAsync(phi_host, p->stage_phi, p->field_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return POISFFT_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return POISFFT_ERR_CUDA;
+  return POISFFT_OK;
+}
+
+int poisfft_check(poisfft_plan* p, void* stream) {
+  if (!p) return POISFFT_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return POISFFT_ERR_CUDA;
+  int h = 0;
+  if (cudaMemcpy(&h, p->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return POISFFT_ERR_CUDA;
+  if (h != 0) {
+    cudaMemset(p->err, 0, sizeof(int));
+    return POISFFT_ERR_TIMEOUT;
+  }
+  return POISFFT_OK;
+}
+
+int poisfft_destroy(poisfft_plan* p) {
+  free_plan(p);
+  return POISFFT_OK;
+}
+
+int poisfft_profile_enable(poisfft_plan* p, int enable) {
+  if (!p) return POISFFT_ERR_INVALID_ARG;
+  p->profiling = enable != 0;
+  return POISFFT_OK;
+}
+
+int poisfft_profile_read(poisfft_plan* p, double* ms, int cap, int* nlaunch, int* nsolves) {
+  if (!p || !nlaunch || !nsolves || (cap > 0 && !ms)) return POISFFT_ERR_INVALID_ARG;
+  const int nl = (int)p->sweeps.size();
+  const int per = nl + 1;
+  const int ns = (int)(p->events.size() / per);
+  *nlaunch = nl;
+  *nsolves = ns;
+  for (int i = 0; i < cap && i < nl; i++) ms[i] = 0.0;
+  int rc = POISFFT_OK;
+  if (ns > 0 && cudaEventSynchronize(p->events[(size_t)ns * per - 1]) != cudaSuccess) rc = POISFFT_ERR_CUDA;
+  for (int s = 0; s < ns && rc == POISFFT_OK; s++)
+    for (int i = 0; i < nl && i < cap; i++) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, p->events[(size_t)s * per + i], p->events[(size_t)s * per + i + 1]) != cudaSuccess) {
+        rc = POISFFT_ERR_CUDA;
+        break;
+      }
+      ms[i] += t;
+    }
+  for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+  p->events.clear();
+  return rc;
+}
+
+int poisfft_launch_info(const poisfft_plan* p, int i, int64_t out[4]) {
+  if (!p || !out || i < 0 || i >= (int)p->sweeps.size()) return POISFFT_ERR_INVALID_ARG;
+  const SweepLaunch& L = p->sweeps[i];
+  out[0] = L.bytes;
+  out[1] = L.kind;
+  out[2] = L.kind == 0 ? L.xa.mode : L.sa.mode;
+  out[3] = L.kind == 0 ? 0 : L.sa.axis_dim;
+  return POISFFT_OK;
+}
+
+int poisfft_plan_info(const poisfft_plan* p, int64_t info[4]) {
+  if (!p || !info) return POISFFT_ERR_INVALID_ARG;
+  info[0] = (int64_t)p->sweeps.size();
+  info[1] = (int64_t)p->ws_bytes;
+  int64_t best = -1, idx = 0;
+  for (size_t i = 0; i < p->sweeps.size(); i++)
+    if (p->sweeps[i].bytes > best) { best = p->sweeps[i].bytes; idx = (int64_t)i; }
+  info[2] = best;
+  info[3] = idx;
+  return POISFFT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,255 @@
+// Sweep kernels of the direct Poisson solve (Sec. 2.1 algorithm, Sec. 2.3
+// multi-D sequence of 1D transforms).
+//
+//   x_sweep        contiguous axis.  Two field rows per complex line.
+//                  Periodic x: R2C / C2R through the two-for-one split
+//                  A_k = (Z_k + conj Z_{n-k})/2, B_k = (Z_k - conj Z_{n-k})/(2i).
+//   strided_sweep  y or z axis of the workspace.  The tile [axis x w columns]
+//                  arrives in shared memory by TMA (cp.async.bulk.tensor, one
+//                  box of up to 256 axis rows per copy, no multicast), is
+//                  transformed in place and written back with coalesced
+//                  row stores.  Mode 2 fuses forward transform, the eigenvalue
+//                  divide of step 2 (with the zero-mode fix) and the backward
+//                  transform, so the last axis costs one HBM round trip.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft_engine.cuh"
+#include "internal.h"
+
+namespace pf {
+
+template <typename T> struct Emax;
+template <> struct Emax<float> { static constexpr int value = 32; };
+template <> struct Emax<double> { static constexpr int value = 16; };
+
+// ---------------------------------------------------------------------------
+// contiguous (x) sweep
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 2) x_sweep_kernel(const XArgs a) {
+  constexpr int EMAX = Emax<T>::value;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
+  const RowTile lay{a.ld};
+  cx<T>* scratch = buf + (size_t)a.lines * a.ld;  // used only by direct-DFT passes
+  const cx<T>* tables = reinterpret_cast<const cx<T>*>(a.tables);
+  const cx<T>* mk = a.ax.mk_off >= 0 ? tables + a.ax.mk_off : nullptr;
+  const int* perm = a.perm;
+  const int nx = a.nx;
+  const int M = a.ax.fft.M;
+  const long long row0 = (long long)blockIdx.x * 2 * a.lines;
+  const int kind = a.mode == 0 ? a.ax.kfwd : a.ax.kinv;
+
+  // ---- stage A: bring the source lines into smem
+  if (a.mode == 0 || !a.r2c) {
+    // complex line (row a, row b) in source order
+    const T* src = reinterpret_cast<const T*>(a.mode == 0 ? a.g : a.ws);
+    const long long ld = a.mode == 0 ? (long long)nx : a.ws_ld;
+    const int total = a.lines * nx;
+    for (int e = threadIdx.x; e < total; e += kThreads) {
+      const int l = e / nx;
+      const int j = e - l * nx;
+      const long long ra = row0 + 2 * l, rb = ra + 1;
+      const T va = ra < a.nrows ? src[ra * ld + j] : T(0);
+      const T vb = rb < a.nrows ? src[rb * ld + j] : T(0);
+      buf[lay.idx(j, l)] = mkc<T>(va, vb);
+    }
+  } else {
+    // C2R assembly: Z_k = A_k + i B_k and Z_{n-k} = conj(A_k) + i conj(B_k)
+    const cx<T>* src = reinterpret_cast<const cx<T>*>(a.ws);
+    const int nh = nx / 2 + 1;
+    const int total = a.lines * nh;
+    for (int e = threadIdx.x; e < total; e += kThreads) {
+      const int l = e / nh;
+      const int k = e - l * nh;
+      const long long ra = row0 + 2 * l, rb = ra + 1;
+      const cx<T> A = ra < a.nrows ? src[ra * a.ws_ld + k] : czero<T>();
+      const cx<T> B = rb < a.nrows ? src[rb * a.ws_ld + k] : czero<T>();
+      if (k == 0 || 2 * k == nx) {
+        buf[lay.idx(k, l)] = mkc<T>(A.x, B.x);  // Hermitian: real parts only
+      } else {
+        buf[lay.idx(k, l)] = mkc<T>(A.x - B.y, A.y + B.x);
+        buf[lay.idx(nx - k, l)] = mkc<T>(A.x + B.y, B.x - A.y);
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- stage B/C: pre-processing gather and the FFT passes
+  pre_tile<T, EMAX>(buf, lay, kind, nx, M, a.lines, mk);
+  run_passes<T, EMAX>(buf, scratch, lay, a.ax.fft, a.lines, tables, kind_uses_inverse_fft(kind));
+
+  // ---- stage D: post-processing and store
+  if (a.mode == 0 && a.r2c) {
+    cx<T>* dst = reinterpret_cast<cx<T>*>(a.ws);
+    const int nh = nx / 2 + 1;
+    const int total = a.lines * nh;
+    for (int e = threadIdx.x; e < total; e += kThreads) {
+      const int l = e / nh;
+      const int k = e - l * nh;
+      const long long ra = row0 + 2 * l, rb = ra + 1;
+      const cx<T> z1 = buf[lay.idx(perm[k], l)];
+      const cx<T> z2 = buf[lay.idx(perm[k == 0 ? 0 : nx - k], l)];
+      // A = (z1 + conj z2)/2,  B = (z1 - conj z2)/(2i)
+      const cx<T> A = mkc<T>(T(0.5) * (z1.x + z2.x), T(0.5) * (z1.y - z2.y));
+      const cx<T> B = mkc<T>(T(0.5) * (z1.y + z2.y), T(0.5) * (z2.x - z1.x));
+      if (ra < a.nrows) dst[ra * a.ws_ld + k] = A;
+      if (rb < a.nrows) dst[rb * a.ws_ld + k] = B;
+    }
+  } else {
+    T* dst = reinterpret_cast<T*>(a.mode == 0 ? a.ws : a.phi);
+    const long long ld = a.mode == 0 ? a.ws_ld : (long long)nx;
+    const int total = a.lines * nx;
+    for (int e = threadIdx.x; e < total; e += kThreads) {
+      const int l = e / nx;
+      const int k = e - l * nx;
+      const long long ra = row0 + 2 * l, rb = ra + 1;
+      const cx<T> v = post_value<T>(buf, lay, kind, nx, k, l, mk, perm);
+      if (ra < a.nrows) dst[ra * ld + k] = v.x;
+      if (rb < a.nrows) dst[rb * ld + k] = v.y;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// strided (y / z) sweep with TMA-staged tiles
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T eigen_factor(const StridedArgs& a, const T* lin, const T* lax, const T* lout, int kx, int k,
+                                          int o) {
+  if (kx >= a.nx) return T(0);
+  if (a.singular && kx == 0 && k == 0 && o == 0) return T(0);
+  const T den = lin[kx] + lax[k] + lout[o];
+  return T(a.scale) / den;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) strided_sweep_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                 const StridedArgs a) {
+  constexpr int EMAX = Emax<T>::value;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + a.bar_off);
+  const ColTile lay{a.w, a.lw};
+  cx<T>* scratch = buf + (size_t)a.rows_alloc * a.w;  // used only by direct-DFT passes
+  const cx<T>* tables = reinterpret_cast<const cx<T>*>(a.tables);
+  const cx<T>* mk = a.ax.mk_off >= 0 ? tables + a.ax.mk_off : nullptr;
+  const int* perm = a.perm;
+  const int n = a.ax.n;
+  const int M = a.ax.fft.M;
+  const int tcol = blockIdx.x % a.ntile_c;
+  const int outer = blockIdx.x / a.ntile_c;
+  const int c0 = tcol * a.w;
+
+  // ---- stage A: TMA boxes of the tile
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t box_bytes = (uint32_t)(2 * a.w * a.box_h * sizeof(T));
+    mbar_arrive_expect_tx(bar, box_bytes * a.nbox);
+    for (int b = 0; b < a.nbox; b++) {
+      cx<T>* dst = buf + (size_t)b * a.box_h * a.w;
+      if (a.axis_dim == 1)
+        tma_load_3d(dst, &tmap, bar, 2 * c0, b * a.box_h, outer);
+      else
+        tma_load_3d(dst, &tmap, bar, 2 * c0, outer, b * a.box_h);
+    }
+  }
+  const bool ok = mbar_wait_bounded(bar, 0);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) atomicExch(a.err, 1);
+    return;
+  }
+
+  cx<T>* out = reinterpret_cast<cx<T>*>(a.data) + (size_t)outer * a.s_outer + c0;
+  const int ncol_valid = a.ncols - c0 < a.w ? a.ncols - c0 : a.w;
+
+  if (a.mode != 2) {
+    const int kind = a.mode == 0 ? a.ax.kfwd : a.ax.kinv;
+    pre_tile<T, EMAX>(buf, lay, kind, n, M, a.w, mk);
+    run_passes<T, EMAX>(buf, scratch, lay, a.ax.fft, a.w, tables, kind_uses_inverse_fft(kind));
+    const int total = n * a.w;
+    for (int e = threadIdx.x; e < total; e += kThreads) {
+      const int c = e & (a.w - 1);
+      const int k = e >> a.lw;
+      if (c < ncol_valid) out[(size_t)k * a.s_axis + c] = post_value<T>(buf, lay, kind, n, k, c, mk, perm);
+    }
+    return;
+  }
+
+  // ---- fused: forward, divide by the eigenvalues, backward
+  pre_tile<T, EMAX>(buf, lay, a.ax.kfwd, n, M, a.w, mk);
+  run_passes<T, EMAX>(buf, scratch, lay, a.ax.fft, a.w, tables, kind_uses_inverse_fft(a.ax.kfwd));
+  {
+    const T* lin = reinterpret_cast<const T*>(a.lam_in);
+    const T* lax = reinterpret_cast<const T*>(a.lam_ax);
+    const T* lout = reinterpret_cast<const T*>(a.lam_out);
+    cx<T> v[EMAX];
+    const int total = n * a.w;
+#pragma unroll
+    for (int j = 0; j < EMAX; j++) {
+      const int e = threadIdx.x + j * kThreads;
+      if (e < total) {
+        const int c = e & (a.w - 1);
+        const int k = e >> a.lw;
+        cx<T> x = post_value<T>(buf, lay, a.ax.kfwd, n, k, c, mk, perm);
+        const int col = c0 + c;
+        if (a.packed) {
+          x.x *= eigen_factor<T>(a, lin, lax, lout, 2 * col, k, outer);
+          x.y *= eigen_factor<T>(a, lin, lax, lout, 2 * col + 1, k, outer);
+        } else {
+          const T f = eigen_factor<T>(a, lin, lax, lout, col, k, outer);
+          x.x *= f;
+          x.y *= f;
+        }
+        v[j] = x;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < EMAX; j++) {
+      const int e = threadIdx.x + j * kThreads;
+      if (e < total) buf[lay.idx(e >> a.lw, e & (a.w - 1))] = v[j];
+    }
+    __syncthreads();
+  }
+  pre_tile<T, EMAX>(buf, lay, a.ax.kinv, n, M, a.w, mk);
+  run_passes<T, EMAX>(buf, scratch, lay, a.ax.fft, a.w, tables, kind_uses_inverse_fft(a.ax.kinv));
+  const int total = n * a.w;
+  for (int e = threadIdx.x; e < total; e += kThreads) {
+    const int c = e & (a.w - 1);
+    const int k = e >> a.lw;
+    if (c < ncol_valid) out[(size_t)k * a.s_axis + c] = post_value<T>(buf, lay, a.ax.kinv, n, k, c, mk, perm);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_x_sweep(const XArgs& a, unsigned grid, size_t smem, cudaStream_t s) {
+  auto k = x_sweep_kernel<T>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_strided_sweep(const CUtensorMap& map, const StridedArgs& a, unsigned grid, size_t smem,
+                                 cudaStream_t s) {
+  auto k = strided_sweep_kernel<T>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kThreads, smem, s>>>(map, a);
+  return cudaGetLastError();
+}
+
+}  // namespace pf

@@ -1,0 +1,7 @@
+// Strided (TMA-staged) sweep kernel instantiation (float).
+#include "launch.h"
+#include "sweep_kernels.cuh"
+
+namespace pf {
+template cudaError_t launch_strided_sweep<float>(const CUtensorMap&, const StridedArgs&, unsigned, size_t, cudaStream_t);
+}  // namespace pf

@@ -1,0 +1,87 @@
+"""The C-ABI library loads and exports every declared symbol; host-side
+argument validation returns the documented status codes (no GPU needed:
+all checks happen before the first CUDA call)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from tests._lib import ensure_built
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pb():
+    ensure_built()
+    from paper_1409_8116_gb300 import binding
+    return binding
+
+
+def _declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"\b(poisfft_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol(pb):
+    lib = ctypes.CDLL(pb.LIB_PATH)
+    declared = _declared_symbols()
+    assert "poisfft_solve" in declared and "poisfft_plan_create" in declared
+    for name in declared:
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+    assert set(pb.EXPORTED) <= set(declared)
+
+
+def test_status_strings(pb):
+    for st in [0, -1, -2, -3, -4, -5, -6, -7, -8]:
+        assert pb.status_string(st) and pb.status_string(st) != "unknown status"
+    assert pb.status_string(12345) == "unknown status"
+
+
+@pytest.mark.parametrize("args,expect", [
+    (((8, 8, 8), (1, 1, 1), (0, 0, 0), 1, 0), None),                 # valid -> CUDA error without GPU, OK with
+    (((8, 8, 8), (1, 1, 1), (0, 0, 0), 7, 0), -1),                   # bad approx
+    (((8, 8, 8), (1, 1, 1), (0, 0, 0), 1, 5), -1),                   # bad dtype
+    (((8, 0, 8), (1, 1, 1), (0, 0, 0), 1, 0), -1),                   # n < 1
+    (((8, 8, 8), (1, -1, 1), (0, 0, 0), 1, 0), -1),                  # L <= 0
+    (((8, 8, 8), (1, 1, 1), (0, 9, 0), 1, 0), -1),                   # bad bc code
+    (((8, 1, 8), (1, 1, 1), (0, 3, 0), 1, 0), -1),                   # NR needs n >= 2
+    (((8, 8, 8), (1, 1, 1), (0, 0, 2, 4, 0, 0), 1, 0), -2),          # faces of one axis differ
+    (((8, 8, 8), (1, 1, 1), (0, 0, 0, 0, 0, 3), 1, 0), -2),
+    (((8, 8, 8), (1, 1, 1), (2, 0, 4), 1, 0), -8),                   # x non-periodic with periodic y
+    (((8, 8, 8), (1, 1, 1), (4, 4, 0), 1, 0), -8),                   # x non-periodic with periodic z
+])
+def test_plan_create_validation(pb, args, expect):
+    rc, plan = pb.plan_create(*args)
+    if expect is None:
+        assert rc in (pb.OK, pb.ERR_CUDA)
+        if rc == pb.OK:
+            pb.destroy(plan)
+    else:
+        assert rc == expect
+        assert not plan.value
+
+
+def test_dims_out_of_range(pb):
+    plan = ctypes.c_void_p()
+    n = (ctypes.c_int64 * 4)(4, 4, 4, 4)
+    L = (ctypes.c_double * 4)(1, 1, 1, 1)
+    bc = (ctypes.c_int * 8)(*([0] * 8))
+    assert pb.lib.poisfft_plan_create(ctypes.byref(plan), 4, n, L, bc, 1, 0) == pb.ERR_INVALID_ARG
+    assert pb.lib.poisfft_plan_create(ctypes.byref(plan), 0, n, L, bc, 1, 0) == pb.ERR_INVALID_ARG
+    assert pb.lib.poisfft_plan_create(None, 3, n, L, bc, 1, 0) == pb.ERR_INVALID_ARG
+
+
+def test_null_plan_calls(pb):
+    assert pb.lib.poisfft_solve(None, None, None, None) == pb.ERR_INVALID_ARG
+    assert pb.lib.poisfft_solve_host(None, None, None, None) == pb.ERR_INVALID_ARG
+    assert pb.lib.poisfft_check(None, None) == pb.ERR_INVALID_ARG
+    assert pb.lib.poisfft_destroy(None) == pb.OK
+    info = (ctypes.c_int64 * 4)()
+    assert pb.lib.poisfft_plan_info(None, info) == pb.ERR_INVALID_ARG

@@ -99,6 +99,11 @@ WORKLOADS = {
     "mixed_fd2_256_f32": dict(
         n=(256, 256, 256), bcs=(P, DS, NS), Ls=(1.0, 1.0, 1.0), approx=FD2,
         dtype="f32", gen=("normal_meanfree", 2)),
+    # 512^3 FP32 FD2, periodic x,y, staggered Neumann z: a profiling-size case
+    # of the 1024^3 workload (fits a few GB on the device, still >> L2)
+    "ppn_fd2_512_f32": dict(
+        n=(512, 512, 512), bcs=(P, P, NS), Ls=(1.0, 1.0, 1.0), approx=FD2,
+        dtype="f32", gen=("normal_meanfree", 3)),
     # 1024^3 FP32 FD2, periodic x,y, staggered Neumann z, L = 1 per axis
     "ppn_fd2_1024_f32": dict(
         n=(1024, 1024, 1024), bcs=(P, P, NS), Ls=(1.0, 1.0, 1.0), approx=FD2,
