@@ -116,6 +116,32 @@ const char* poisfft_status_string(int status);
  * Returns POISFFT_OK or POISFFT_ERR_INVALID_ARG. */
 int poisfft_plan_info(const poisfft_plan* plan, int64_t info[4]);
 
+/* Solve one problem without allocating device memory.  The paper has no
+ * counterpart; this entry point exists for callers that cannot call
+ * cudaMalloc -- code inside a framework that owns all device memory through
+ * its own pool or budget, plug-ins whose device footprint is fixed after
+ * start-up, or paths that must avoid the implicit synchronisation of an
+ * allocation.  It runs the same sweep kernels as poisfft_solve (arguments as
+ * in poisfft_plan_create plus phi, g, stream as in poisfft_solve) but keeps
+ * workspace, tables and error flag in one file-scope device array of
+ * 32 MiB that every GPU loading this library holds until the process exits.
+ *   - Sizes whose workspace and tables exceed 32 MiB return
+ *     POISFFT_ERR_UNSUPPORTED_SIZE before any CUDA call (FP32: up to about
+ *     200^3 or 2048^2 with a periodic x axis).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents; each
+ *     call clears what must start at zero.  Calls that overlap on the GPU
+ *     (other streams, other host threads) race on the array: serialise them.
+ *   - Tables are copied from pageable host memory, so the call waits for
+ *     the work already queued on `stream` before it returns.
+ * Returns the status codes of poisfft_plan_create / poisfft_solve; check
+ * the kernels' bounded waits with cudaStreamSynchronize (no plan exists
+ * for poisfft_check). */
+int poisfft_solve_noalloc(int dims, const int64_t n[], const double L[], const int bc[], int approx, int dtype,
+                          void* phi, const void* g, void* stream);
+
 /* Per-launch timing for benchmarks (no paper counterpart; measurement aid).
  * When enabled, every solve records a CUDA event on its stream before each
  * kernel launch and after the last one.  Host cost: one event record per

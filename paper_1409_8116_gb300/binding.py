@@ -42,6 +42,7 @@ EXPORTED = [
     "poisfft_profile_enable",
     "poisfft_profile_read",
     "poisfft_launch_info",
+    "poisfft_solve_noalloc",
 ]
 
 
@@ -80,6 +81,10 @@ def _load():
     lib.poisfft_profile_read.restype = ctypes.c_int
     lib.poisfft_launch_info.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p]
     lib.poisfft_launch_info.restype = ctypes.c_int
+    lib.poisfft_solve_noalloc.argtypes = [ctypes.c_int, i64p, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.poisfft_solve_noalloc.restype = ctypes.c_int
     return lib
 
 
@@ -132,6 +137,18 @@ def solve(plan, phi, g, stream=None):
 
 def solve_host(plan, phi, g, stream=None):
     return lib.poisfft_solve_host(plan, _ptr(phi), _ptr(g), _stream(stream))
+
+
+def solve_noalloc(n, L, bc, approx, dtype, phi, g, stream=None):
+    """poisfft_solve_noalloc: one solve with no device allocation (workspace in
+    the library's fixed 32 MiB device array).  Returns the status code."""
+    dims = len(n)
+    faces = [b for b in bc for _ in (0, 1)] if len(bc) == dims else list(bc)
+    n_arr = (ctypes.c_int64 * dims)(*[int(v) for v in n])
+    L_arr = (ctypes.c_double * dims)(*[float(v) for v in L])
+    bc_arr = (ctypes.c_int * len(faces))(*[int(v) for v in faces])
+    return lib.poisfft_solve_noalloc(dims, n_arr, L_arr, bc_arr, int(approx), int(dtype), _ptr(phi), _ptr(g),
+                                     _stream(stream))
 
 
 def check(plan, stream=None):

@@ -17,6 +17,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -683,3 +684,189 @@ int poisfft_plan_info(const poisfft_plan* p, int64_t info[4]) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Solve without device allocation
+// ---------------------------------------------------------------------------
+// Some callers cannot call cudaMalloc: code running under a framework that
+// owns all device memory through its own pool or budget, plug-ins that may
+// not change the device footprint after start-up, or code paths that must
+// not trigger an implicit device synchronisation.  For them,
+// poisfft_solve_noalloc solves one problem with the same sweep kernels, but
+// its workspace, tables and error flag live in the file-scope array below,
+// which every GPU that loads this library holds until the process exits.
+namespace {
+
+constexpr size_t kNoAllocBytes = 32u << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mutex;
+
+// Device address of g_noalloc_scratch on the current device (set-up once per
+// device; the host-side symbol itself is not a device address).
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return POISFFT_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return POISFFT_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return POISFFT_OK;
+}
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+template <typename T>
+int noalloc_upload(poisfft_plan* p, unsigned char* base, size_t& off, cudaStream_t st) {
+  for (int a = 0; a < 3; a++) {
+    AxisPlan& ax = p->axes[a];
+    const size_t nt = ax.tab_re.size();
+    std::vector<T> tab(2 * nt);
+    for (size_t i = 0; i < nt; i++) { tab[2 * i] = (T)ax.tab_re[i]; tab[2 * i + 1] = (T)ax.tab_im[i]; }
+    std::vector<T> lam(std::max<size_t>(ax.lam.size(), 1), T(0));
+    for (size_t i = 0; i < ax.lam.size(); i++) lam[i] = (T)ax.lam[i];
+    p->tables[a] = base + off;
+    off = align256(off + tab.size() * sizeof(T));
+    p->lam[a] = base + off;
+    off = align256(off + lam.size() * sizeof(T));
+    p->perm[a] = reinterpret_cast<int*>(base + off);
+    off = align256(off + ax.perm.size() * sizeof(int));
+    if (off > kNoAllocBytes) return POISFFT_ERR_UNSUPPORTED_SIZE;
+    // pageable sources: each copy has consumed its host buffer when it returns
+    if (cudaMemcpyAsync(p->tables[a], tab.data(), tab.size() * sizeof(T), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(p->lam[a], lam.data(), lam.size() * sizeof(T), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(p->perm[a], ax.perm.data(), ax.perm.size() * sizeof(int), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess)
+      return POISFFT_ERR_CUDA;
+  }
+  return POISFFT_OK;
+}
+
+// Forget the carved-out pointers, then free the host-side plan object.
+void release_noalloc_plan(poisfft_plan* p) {
+  p->ws = nullptr;
+  p->err = nullptr;
+  for (int a = 0; a < 3; a++) {
+    p->tables[a] = nullptr;
+    p->lam[a] = nullptr;
+    p->perm[a] = nullptr;
+  }
+  delete p;
+}
+
+}  // namespace
+
+extern "C" int poisfft_solve_noalloc(int dims, const int64_t n[], const double L[], const int bc[], int approx,
+                                     int dtype, void* phi, const void* g, void* stream) {
+  if (!n || !L || !bc || !phi || !g || dims < 1 || dims > 3) return POISFFT_ERR_INVALID_ARG;
+  if (approx != POISFFT_SPECTRAL && approx != POISFFT_FD2) return POISFFT_ERR_INVALID_ARG;
+  if (dtype != POISFFT_F32 && dtype != POISFFT_F64) return POISFFT_ERR_INVALID_ARG;
+  int bca[3] = {POISFFT_P, POISFFT_P, POISFFT_P};
+  long long nn[3] = {1, 1, 1};
+  double LL[3] = {1.0, 1.0, 1.0};
+  for (int a = 0; a < dims; a++) {
+    if (n[a] < 1 || n[a] > (1 << 24)) return POISFFT_ERR_INVALID_ARG;
+    if (!(L[a] > 0.0) || !isfinite(L[a])) return POISFFT_ERR_INVALID_ARG;
+    const int b0 = bc[2 * a], b1 = bc[2 * a + 1];
+    if (b0 < POISFFT_P || b0 > POISFFT_NS || b1 < POISFFT_P || b1 > POISFFT_NS) return POISFFT_ERR_INVALID_ARG;
+    if (b0 != b1) return POISFFT_ERR_UNSUPPORTED_BC;
+    if (b0 == POISFFT_NR && n[a] < 2) return POISFFT_ERR_INVALID_ARG;
+    bca[a] = b0;
+    nn[a] = n[a];
+    LL[a] = L[a];
+  }
+  const size_t esize = dtype == POISFFT_F32 ? 4 : 8;
+  if (((uintptr_t)phi % esize) != 0 || ((uintptr_t)g % esize) != 0) return POISFFT_ERR_MISALIGNED;
+  const bool xper = bca[0] == POISFFT_P;
+  bool any_per_yz = false;
+  for (int a = 1; a < dims; a++) any_per_yz |= bca[a] == POISFFT_P;
+  if (!xper && any_per_yz) return POISFFT_ERR_NOT_IMPLEMENTED;
+  // workspace size before any host planning: reject what cannot fit
+  const long long ncols0 = xper ? nn[0] / 2 + 1 : (nn[0] + 1) / 2;
+  const long long pitch0 = (ncols0 + 1) / 2 * 2;
+  const double ws_need = (double)pitch0 * 2 * esize * nn[1] * nn[2];
+  if (ws_need + 256 > (double)kNoAllocBytes) return POISFFT_ERR_UNSUPPORTED_SIZE;
+
+  poisfft_plan* p = new (std::nothrow) poisfft_plan();
+  if (!p) return POISFFT_ERR_ALLOC;
+  p->dims = dims;
+  p->dtype = dtype;
+  p->approx = approx;
+  p->nx = (int)nn[0];
+  p->ny = (int)nn[1];
+  p->nz = (int)nn[2];
+  p->esize = esize;
+  p->r2c = xper ? 1 : 0;
+  const int emax = dtype == POISFFT_F32 ? 32 : 16;
+  bool sing = true;
+  int rc = POISFFT_OK;
+  for (int a = 0; a < 3 && rc == POISFFT_OK; a++) {
+    const bool null_axis = a >= dims;
+    rc = build_axis(p->axes[a], bca[a], (int)nn[a], LL[a], approx, emax, null_axis);
+    if (!null_axis) sing = sing && (bca[a] == POISFFT_P || bca[a] == POISFFT_NR || bca[a] == POISFFT_NS);
+  }
+  if (rc != POISFFT_OK) { release_noalloc_plan(p); return rc; }
+  p->singular = sing ? 1 : 0;
+  p->ncols = (int)ncols0;
+  p->pitch = (int)pitch0;
+  p->ws_bytes = (size_t)p->pitch * 2 * p->esize * p->ny * p->nz;
+
+  std::vector<SweepLaunch> sw;
+  SweepLaunch Ls;
+  const int fused_axis = dims == 3 ? 2 : 1;
+  if ((rc = plan_x_sweep(p, 0, Ls)) == POISFFT_OK) sw.push_back(Ls);
+  if (rc == POISFFT_OK && dims == 3 && (rc = plan_strided_sweep(p, 1, 0, Ls)) == POISFFT_OK) sw.push_back(Ls);
+  if (rc == POISFFT_OK && (rc = plan_strided_sweep(p, fused_axis, 2, Ls)) == POISFFT_OK) sw.push_back(Ls);
+  if (rc == POISFFT_OK && dims == 3 && (rc = plan_strided_sweep(p, 1, 1, Ls)) == POISFFT_OK) sw.push_back(Ls);
+  if (rc == POISFFT_OK && (rc = plan_x_sweep(p, 1, Ls)) == POISFFT_OK) sw.push_back(Ls);
+  if (rc != POISFFT_OK) { release_noalloc_plan(p); return rc; }
+  p->sweeps = sw;
+
+  // carve the scratch array: error flag | tables per axis | workspace
+  void* scratch = nullptr;
+  if ((rc = noalloc_scratch(&scratch)) != POISFFT_OK) { release_noalloc_plan(p); return rc; }
+  unsigned char* base = static_cast<unsigned char*>(scratch);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  size_t off = 0;
+  p->err = reinterpret_cast<int*>(base);
+  off = 256;
+  rc = esize == 4 ? noalloc_upload<float>(p, base, off, st) : noalloc_upload<double>(p, base, off, st);
+  if (rc == POISFFT_OK && off + p->ws_bytes > kNoAllocBytes) rc = POISFFT_ERR_UNSUPPORTED_SIZE;
+  if (rc != POISFFT_OK) { cudaGetLastError(); release_noalloc_plan(p); return rc; }
+  p->ws = base + off;
+  // the array keeps the previous call's contents: zero the flag and the workspace
+  if (cudaMemsetAsync(p->err, 0, sizeof(int), st) != cudaSuccess ||
+      cudaMemsetAsync(p->ws, 0, p->ws_bytes, st) != cudaSuccess) {
+    release_noalloc_plan(p);
+    return POISFFT_ERR_CUDA;
+  }
+  for (auto& Lw : p->sweeps) {
+    if (Lw.kind == 0) {
+      Lw.xa.tables = p->tables[0];
+      Lw.xa.perm = p->perm[0];
+      Lw.xa.ws = p->ws;
+      Lw.xa.err = p->err;
+    } else {
+      const int a = Lw.sa.axis_dim;
+      Lw.sa.tables = p->tables[a];
+      Lw.sa.perm = p->perm[a];
+      Lw.sa.data = p->ws;
+      Lw.sa.lam_in = p->lam[0];
+      Lw.sa.lam_ax = p->lam[a];
+      Lw.sa.lam_out = p->lam[a == 1 ? 2 : 1];
+      Lw.sa.err = p->err;
+    }
+  }
+  if ((rc = encode_maps(p)) == POISFFT_OK)
+    rc = esize == 4 ? enqueue<float>(p, phi, g, st) : enqueue<double>(p, phi, g, st);
+  release_noalloc_plan(p);
+  return rc;
+}
