@@ -1,0 +1,83 @@
+// Instantiations and dispatch of the specialised two-pass FP32 kernels.
+#include "fast_kernels.cuh"
+#include "launch.h"
+
+namespace pf {
+
+namespace {
+
+template <int R1, int R2, int W, int MODE, int KIND>
+cudaError_t run_strided(const CUtensorMap& map, const fast::FastStridedArgs& a, unsigned grid, size_t smem,
+                        cudaStream_t s) {
+  auto k = fast::fast_strided_kernel<R1, R2, W, MODE, KIND>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, W * fast::Shape<R1, R2>::RMAX, smem, s>>>(map, a);
+  return cudaGetLastError();
+}
+
+template <int R1, int R2, int W>
+cudaError_t run_strided_mk(int mode, int kind, const CUtensorMap& map, const fast::FastStridedArgs& a, unsigned grid,
+                           size_t smem, cudaStream_t s) {
+  using namespace fast;
+  if (kind == FK_DFT) {
+    if (mode == FM_FWD) return run_strided<R1, R2, W, FM_FWD, FK_DFT>(map, a, grid, smem, s);
+    if (mode == FM_INV) return run_strided<R1, R2, W, FM_INV, FK_DFT>(map, a, grid, smem, s);
+    return run_strided<R1, R2, W, FM_FUSED, FK_DFT>(map, a, grid, smem, s);
+  }
+  if (mode == FM_FWD) return run_strided<R1, R2, W, FM_FWD, FK_DCT>(map, a, grid, smem, s);
+  if (mode == FM_INV) return run_strided<R1, R2, W, FM_INV, FK_DCT>(map, a, grid, smem, s);
+  return run_strided<R1, R2, W, FM_FUSED, FK_DCT>(map, a, grid, smem, s);
+}
+
+template <int R1, int R2, int MODE>
+cudaError_t run_x(const fast::FastXArgs& a, unsigned grid, size_t smem, cudaStream_t s) {
+  auto k = fast::fast_x_kernel<R1, R2, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, 256, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int R1, int R2>
+cudaError_t run_x_m(int mode, const fast::FastXArgs& a, unsigned grid, size_t smem, cudaStream_t s) {
+  return mode == fast::FM_FWD ? run_x<R1, R2, fast::FM_FWD>(a, grid, smem, s) : run_x<R1, R2, fast::FM_INV>(a, grid, smem, s);
+}
+
+}  // namespace
+
+bool fast_shape(int M, int* R1, int* R2, int* W) {
+  switch (M) {
+    case 64: *R1 = 8; *R2 = 8; *W = 32; return true;
+    case 128: *R1 = 16; *R2 = 8; *W = 16; return true;
+    case 256: *R1 = 16; *R2 = 16; *W = 16; return true;
+    case 512: *R1 = 32; *R2 = 16; *W = 8; return true;
+    case 1024: *R1 = 32; *R2 = 32; *W = 8; return true;
+    default: return false;
+  }
+}
+
+cudaError_t launch_fast_strided(int M, int mode, int kind, const CUtensorMap& map, const fast::FastStridedArgs& a,
+                                unsigned grid, size_t smem, cudaStream_t s) {
+  switch (M) {
+    case 64: return run_strided_mk<8, 8, 32>(mode, kind, map, a, grid, smem, s);
+    case 128: return run_strided_mk<16, 8, 16>(mode, kind, map, a, grid, smem, s);
+    case 256: return run_strided_mk<16, 16, 16>(mode, kind, map, a, grid, smem, s);
+    case 512: return run_strided_mk<32, 16, 8>(mode, kind, map, a, grid, smem, s);
+    case 1024: return run_strided_mk<32, 32, 8>(mode, kind, map, a, grid, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_fast_x(int M, int mode, const fast::FastXArgs& a, unsigned grid, size_t smem, cudaStream_t s) {
+  switch (M) {
+    case 64: return run_x_m<8, 8>(mode, a, grid, smem, s);
+    case 128: return run_x_m<16, 8>(mode, a, grid, smem, s);
+    case 256: return run_x_m<16, 16>(mode, a, grid, smem, s);
+    case 512: return run_x_m<32, 16>(mode, a, grid, smem, s);
+    case 1024: return run_x_m<32, 32>(mode, a, grid, smem, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace pf

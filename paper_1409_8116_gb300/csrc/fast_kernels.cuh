@@ -1,0 +1,401 @@
+// Specialised sweep kernels for two-pass power-of-two lines (FP32).
+//
+// Line length M = R1 * R2 with R1, R2 in {8, 16, 32} (M = 64 ... 1024).
+// Forward transforms are decimation in frequency (DIF), backward transforms
+// decimation in time (DIT), so no pass reorders data:
+//   DIF pass 1 (radix R1): butterfly j < R2 takes points j + R2*q, DFT,
+//     twiddle exp(-2 pi i j s / M) on output s, stores it at block s, row j.
+//   DIF pass 2 (radix R2): butterfly b < R1 takes block b; its output s2 is
+//     the DFT coefficient k = b + R1*s2 (digit-reversed arrangement).
+//   DIT pass A (radix R2) consumes that arrangement block by block, DIT pass B
+//     (radix R1, twiddle before the butterfly) returns natural order.
+// After pass 1 the tile sits in a padded layout (64 bytes after every block
+// of R2 rows) so that pass 2 reads whole blocks without bank conflicts.
+//
+// Axes with DCT-II / DCT-III (Neumann staggered) and DST-II / DST-III
+// (Dirichlet staggered) use the even/odd reordering of Makhoul (1980): the
+// x sweeps store grid plane j of such an axis at plane position
+// j/2 (j even) or n-1-(j-1)/2 (j odd), times (-1)^j for DST-II, so the
+// strided sweep sees the reordered sequence directly; the backward sweep
+// leaves its result in that order and the x backward sweep reads it back.
+// The spectrum of those axes is stored in DCT-II index order (for DST-II the
+// eigenvalue table is reversed accordingly).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft_engine.cuh"
+#include "internal.h"
+
+namespace pf {
+namespace fast {
+
+enum FastKind : int { FK_DFT = 0, FK_DCT = 1 };
+enum FastMode : int { FM_FWD = 0, FM_INV = 1, FM_FUSED = 2 };
+
+struct FastStridedArgs {
+  const float2* tw;        // tw[s * R2 + j] = exp(-2 pi i j s / M), s < R1, j < R2
+  const float2* mk;        // exp(-i pi k / (2M)), k < M (DCT axes)
+  const float* lam_in;     // x eigenvalues by column
+  const float* lam_ax;     // swept-axis eigenvalues in storage order
+  const float* lam_out;    // outer-axis eigenvalues in storage order
+  float scale;
+  int singular;
+  int ncols;               // valid complex columns
+  int ntile_c;
+  int box_h, nbox;
+  int axis_dim;            // 1: y, 2: z (tensor-map dimension of the swept axis)
+  long long s_axis, s_outer;
+  float2* data;
+  int* err;
+};
+
+struct FastXArgs {
+  const float2* tw;        // as above for the x line
+  int nx;                  // = M
+  int lines;               // line pairs per CTA
+  long long nrows;         // ny * nz
+  int ny, nz;
+  int perm_y, perm_z;      // 1: plane reordering along that axis (DCT/DST axes)
+  int sign_y, sign_z;      // 1: (-1)^j sign along that axis (DST axes)
+  long long ws_ld;         // workspace row stride (complex)
+  const float* g;
+  float* phi;
+  float2* ws;
+};
+
+// position of grid plane j in the even/odd reordering of an axis of length n
+__device__ __forceinline__ int makhoul_pos(int j, int n) { return (j & 1) ? n - 1 - (j >> 1) : (j >> 1); }
+
+template <int R1, int R2>
+struct Shape {
+  static constexpr int M = R1 * R2;
+  static constexpr int RMAX = R1 > R2 ? R1 : R2;
+};
+
+// ---------------------------------------------------------------------------
+// strided sweep
+// ---------------------------------------------------------------------------
+// Tile: W columns x M rows.  Thread t: column c = t % W, butterfly index
+// t / W.  Smem: TMA layout row*W + c, then padded layout
+// block*(R2*W + 8) + row*W + c.
+template <int R1, int R2, int W, int MODE, int KIND>
+__global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, 2)
+    fast_strided_kernel(const __grid_constant__ CUtensorMap tmap, const FastStridedArgs a) {
+  constexpr int M = R1 * R2;
+  constexpr int NT = W * Shape<R1, R2>::RMAX;
+  constexpr int BS = R2 * W + 8;  // padded block stride (complex)
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  constexpr int TILE_C = (R1 * BS > M * W) ? R1 * BS : M * W;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + ((TILE_C * 8 + 15) / 16) * 16);
+
+  const int tid = threadIdx.x;
+  const int c = tid % W;
+  const int bi = tid / W;  // butterfly index within the column
+  const int tcol = blockIdx.x % a.ntile_c;
+  const int outer = blockIdx.x / a.ntile_c;
+  const int c0 = tcol * W;
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t box_bytes = (uint32_t)(2 * W * a.box_h * sizeof(float));
+    mbar_arrive_expect_tx(bar, box_bytes * a.nbox);
+    for (int b = 0; b < a.nbox; b++) {
+      float2* dst = sm + (size_t)b * a.box_h * W;
+      if (a.axis_dim == 1)
+        tma_load_3d(dst, &tmap, bar, 2 * c0, b * a.box_h, outer);
+      else
+        tma_load_3d(dst, &tmap, bar, 2 * c0, outer, b * a.box_h);
+    }
+  }
+  const bool ok = mbar_wait_bounded(bar, 0);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) atomicExch(a.err, 1);
+    return;
+  }
+
+  float2* out = a.data + (size_t)outer * a.s_outer + c0;
+  const bool col_ok = c0 + c < a.ncols;
+
+  if (MODE == FM_FWD || MODE == FM_FUSED) {
+    // ---- DIF pass 1 from the TMA layout
+    float2 u[R1];
+    const bool act1 = bi < R2;
+    const int j = bi;
+    if (act1) {
+#pragma unroll
+      for (int q = 0; q < R1; q++) u[q] = sm[(j + R2 * q) * W + c];
+    }
+    __syncthreads();
+    if (act1) {
+      Dft<float, R1, false>::run(u);
+      if (j != 0) {
+#pragma unroll
+        for (int s = 1; s < R1; s++) u[s] = cmul<float>(u[s], __ldg(&a.tw[s * R2 + j]));
+      }
+#pragma unroll
+      for (int s = 0; s < R1; s++) sm[s * BS + j * W + c] = u[s];
+    }
+    __syncthreads();
+
+    // ---- DIF pass 2: thread b holds coefficient k = b + R1*s2 in y[s2]
+    float2 y[R2];
+    const bool act2 = bi < R1;
+    const int b = bi;
+    if (act2) {
+#pragma unroll
+      for (int q = 0; q < R2; q++) y[q] = sm[b * BS + q * W + c];
+      Dft<float, R2, false>::run(y);
+    }
+
+    if (KIND == FK_DCT) {
+      // DCT-II post-processing needs Y_{M-k}: exchange through smem
+      if (act2) {
+#pragma unroll
+        for (int s2 = 0; s2 < R2; s2++) sm[b * BS + s2 * W + c] = y[s2];
+      }
+      __syncthreads();
+    }
+
+    if (MODE == FM_FWD) {
+      if (act2 && col_ok) {
+#pragma unroll
+        for (int s2 = 0; s2 < R2; s2++) {
+          const int k = b + R1 * s2;
+          float2 x = y[s2];
+          if (KIND == FK_DCT) {
+            const int kp = k == 0 ? 0 : M - k;
+            const float2 yp = sm[(kp % R1) * BS + (kp / R1) * W + c];
+            const float2 w = __ldg(&a.mk[k]);
+            x = cadd<float>(cmul<float>(w, x), cmulc<float>(yp, w));  // X_k = w Y_k + conj(w) Y_{M-k}
+          }
+          out[(size_t)k * a.s_axis + c] = x;
+        }
+      }
+      return;
+    }
+
+    // ---- fused: divide by the eigenvalues, then DIT pass A in registers
+    if (act2) {
+      const int col = c0 + c;
+      const float lam_xo = (col < a.ncols ? __ldg(&a.lam_in[col]) : 0.f) + __ldg(&a.lam_out[outer]);
+      const bool zero_row = a.singular && col == 0 && outer == 0;
+#pragma unroll
+      for (int s2 = 0; s2 < R2; s2++) {
+        const int k = b + R1 * s2;
+        if (KIND == FK_DFT) {
+          float f = __fdividef(a.scale, lam_xo + __ldg(&a.lam_ax[k]));
+          if (zero_row && k == 0) f = 0.f;
+          y[s2] = make_float2(y[s2].x * f, y[s2].y * f);
+        } else {
+          // X_k, X_{M-k} from Y_k, Y_{M-k}; scale both; V_k = conj(w_k) (X'_k - i X'_{M-k})
+          const int kp = k == 0 ? 0 : M - k;
+          const float2 yk = y[s2];
+          const float2 yp = sm[(kp % R1) * BS + (kp / R1) * W + c];
+          const float2 w = __ldg(&a.mk[k]);
+          const float2 wy = cmul<float>(w, yk);
+          const float2 cy = cmulc<float>(yp, w);
+          const float2 xk = cadd<float>(wy, cy);
+          float fk = __fdividef(a.scale, lam_xo + __ldg(&a.lam_ax[k]));
+          if (zero_row && k == 0) fk = 0.f;
+          float2 v = make_float2(xk.x * fk, xk.y * fk);
+          if (k != 0) {
+            const float2 xm = mul_i<float>(csub<float>(wy, cy));  // X_{M-k} = i (w Y_k - conj(w) Y_{M-k})
+            const float fm = __fdividef(a.scale, lam_xo + __ldg(&a.lam_ax[kp]));
+            v = make_float2(v.x + xm.y * fm, v.y - xm.x * fm);     // X'_k - i X'_{M-k}
+          }
+          y[s2] = cmulc<float>(v, w);
+        }
+      }
+      Dft<float, R2, true>::run(y);
+    }
+    if (KIND == FK_DCT) __syncthreads();  // partners have read this block
+    if (act2) {
+#pragma unroll
+      for (int s = 0; s < R2; s++) sm[b * BS + s * W + c] = y[s];
+    }
+    __syncthreads();
+  } else {
+    // ---- backward only: DIT pass A from the TMA layout (natural order input)
+    float2 y[R2];
+    const bool act2 = bi < R1;
+    const int b = bi;
+    if (act2) {
+#pragma unroll
+      for (int q = 0; q < R2; q++) {
+        const int k = b + R1 * q;
+        float2 x = sm[k * W + c];
+        if (KIND == FK_DCT) {
+          // V_k = conj(w_k) (X_k - i X_{M-k}), X_M = 0
+          const float2 xm = k == 0 ? make_float2(0.f, 0.f) : sm[(M - k) * W + c];
+          x = cmulc<float>(make_float2(x.x + xm.y, x.y - xm.x), __ldg(&a.mk[k]));
+        }
+        y[q] = x;
+      }
+      Dft<float, R2, true>::run(y);
+    }
+    __syncthreads();
+    if (act2) {
+#pragma unroll
+      for (int s = 0; s < R2; s++) sm[b * BS + s * W + c] = y[s];
+    }
+    __syncthreads();
+  }
+
+  // ---- DIT pass B (radix R1): natural-order output j + R2*s
+  {
+    float2 u[R1];
+    const int j = bi;
+    if (bi < R2 && col_ok) {
+#pragma unroll
+      for (int q = 0; q < R1; q++) u[q] = sm[q * BS + j * W + c];
+      if (j != 0) {
+#pragma unroll
+        for (int q = 1; q < R1; q++) u[q] = cmulc<float>(u[q], __ldg(&a.tw[q * R2 + j]));
+      }
+      Dft<float, R1, true>::run(u);
+#pragma unroll
+      for (int s = 0; s < R1; s++) out[(size_t)(j + R2 * s) * a.s_axis + c] = u[s];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// contiguous (x) sweep, periodic x: R2C / C2R of two rows per complex line
+// ---------------------------------------------------------------------------
+// Thread t: line l = t / RMAX, butterfly index t % RMAX.  Smem per line:
+// R1 blocks of R2 + 1 complex (padded).
+template <int R1, int R2>
+__device__ __forceinline__ int xpos(int k) {  // padded smem position of coefficient k
+  return (k % R1) * (R2 + 1) + k / R1;
+}
+
+__device__ __forceinline__ void ws_row_of(const FastXArgs& a, long long r, long long& wr, float& sg) {
+  int y = (int)(r % a.ny);
+  int z = (int)(r / a.ny);
+  sg = 1.f;
+  if (a.sign_y && (y & 1)) sg = -sg;
+  if (a.sign_z && (z & 1)) sg = -sg;
+  if (a.perm_y) y = makhoul_pos(y, a.ny);
+  if (a.perm_z) z = makhoul_pos(z, a.nz);
+  wr = (long long)z * a.ny + y;
+}
+
+template <int R1, int R2, int MODE>
+__global__ void __launch_bounds__(256, 2) fast_x_kernel(const FastXArgs a) {
+  constexpr int M = R1 * R2;
+  constexpr int RMAX = Shape<R1, R2>::RMAX;
+  constexpr int LS = R1 * (R2 + 1);  // padded line stride (complex)
+  constexpr int LPC = 256 / RMAX;    // lines per CTA
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int l = tid / RMAX;
+  const int bi = tid % RMAX;
+  float2* line = sm + l * LS;
+  const long long ra = ((long long)blockIdx.x * LPC + l) * 2;
+  const long long rb = ra + 1;
+  const bool va = ra < a.nrows, vb = rb < a.nrows;
+  long long wa = 0, wb = 0;
+  float sa = 1.f, sb = 1.f;
+  if (va) ws_row_of(a, ra, wa, sa);
+  if (vb) ws_row_of(a, rb, wb, sb);
+
+  if (MODE == FM_FWD) {
+    // DIF pass 1 straight from global rows a, b
+    if (bi < R2) {
+      const int j = bi;
+      float2 u[R1];
+      const float* ga = a.g + ra * M;
+      const float* gb = a.g + rb * M;
+#pragma unroll
+      for (int q = 0; q < R1; q++) u[q] = make_float2(va ? ga[j + R2 * q] : 0.f, vb ? gb[j + R2 * q] : 0.f);
+      Dft<float, R1, false>::run(u);
+      if (j != 0) {
+#pragma unroll
+        for (int s = 1; s < R1; s++) u[s] = cmul<float>(u[s], __ldg(&a.tw[s * R2 + j]));
+      }
+#pragma unroll
+      for (int s = 0; s < R1; s++) line[s * (R2 + 1) + j] = u[s];
+    }
+    __syncthreads();
+    if (bi < R1) {
+      const int b = bi;
+      float2 y[R2];
+#pragma unroll
+      for (int q = 0; q < R2; q++) y[q] = line[b * (R2 + 1) + q];
+      Dft<float, R2, false>::run(y);
+#pragma unroll
+      for (int s = 0; s < R2; s++) line[b * (R2 + 1) + s] = y[s];
+    }
+    __syncthreads();
+    // split Z into the half spectra of rows a and b
+    constexpr int NH = M / 2 + 1;
+    float2* da = a.ws + wa * a.ws_ld;
+    float2* db = a.ws + wb * a.ws_ld;
+    for (int k = bi; k < NH; k += RMAX) {
+      const float2 z1 = line[xpos<R1, R2>(k)];
+      const float2 z2 = line[xpos<R1, R2>(k == 0 ? 0 : M - k)];
+      const float2 A = make_float2(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y));
+      const float2 B = make_float2(0.5f * (z1.y + z2.y), 0.5f * (z2.x - z1.x));
+      if (va) da[k] = make_float2(sa * A.x, sa * A.y);
+      if (vb) db[k] = make_float2(sb * B.x, sb * B.y);
+    }
+  } else {
+    // C2R assembly into the digit-reversed arrangement
+    constexpr int NH = M / 2 + 1;
+    const float2* sa_p = a.ws + wa * a.ws_ld;
+    const float2* sb_p = a.ws + wb * a.ws_ld;
+    for (int k = bi; k < NH; k += RMAX) {
+      float2 A = va ? sa_p[k] : make_float2(0.f, 0.f);
+      float2 B = vb ? sb_p[k] : make_float2(0.f, 0.f);
+      A = make_float2(sa * A.x, sa * A.y);
+      B = make_float2(sb * B.x, sb * B.y);
+      if (k == 0 || 2 * k == M) {
+        line[xpos<R1, R2>(k)] = make_float2(A.x, B.x);
+      } else {
+        line[xpos<R1, R2>(k)] = make_float2(A.x - B.y, A.y + B.x);
+        line[xpos<R1, R2>(M - k)] = make_float2(A.x + B.y, B.x - A.y);
+      }
+    }
+    __syncthreads();
+    if (bi < R1) {
+      const int b = bi;
+      float2 y[R2];
+#pragma unroll
+      for (int q = 0; q < R2; q++) y[q] = line[b * (R2 + 1) + q];
+      Dft<float, R2, true>::run(y);
+#pragma unroll
+      for (int s = 0; s < R2; s++) line[b * (R2 + 1) + s] = y[s];
+    }
+    __syncthreads();
+    if (bi < R2) {
+      const int j = bi;
+      float2 u[R1];
+#pragma unroll
+      for (int q = 0; q < R1; q++) u[q] = line[q * (R2 + 1) + j];
+      if (j != 0) {
+#pragma unroll
+        for (int q = 1; q < R1; q++) u[q] = cmulc<float>(u[q], __ldg(&a.tw[q * R2 + j]));
+      }
+      Dft<float, R1, true>::run(u);
+      float* pa = a.phi + ra * M;
+      float* pb = a.phi + rb * M;
+#pragma unroll
+      for (int s = 0; s < R1; s++) {
+        if (va) pa[j + R2 * s] = u[s].x;
+        if (vb) pb[j + R2 * s] = u[s].y;
+      }
+    }
+  }
+}
+
+}  // namespace fast
+}  // namespace pf

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "../../include/poisfft.h"
+#include "fast_kernels.cuh"
 #include "internal.h"
 #include "launch.h"
 
@@ -213,9 +214,12 @@ int build_axis(AxisPlan& ax, int bc, int n, double L, int approx, int emax, bool
 }
 
 struct SweepLaunch {
-  int kind;               // 0 x sweep, 1 strided sweep
+  int kind;               // 0 x sweep, 1 strided sweep, 2 fast x sweep, 3 fast strided sweep
   XArgs xa;
   StridedArgs sa;
+  fast::FastXArgs fxa;
+  fast::FastStridedArgs fsa;
+  int M, fmode, fkind, axis, w, box_h;  // fast sweeps
   int map;                // tensor map index (strided)
   unsigned grid;
   size_t smem;
@@ -280,6 +284,10 @@ struct poisfft_plan {
   size_t field_bytes = 0;
   bool profiling = false;
   std::vector<cudaEvent_t> events;   // (launches + 1) per profiled solve
+  bool fast = false;                 // specialised two-pass FP32 kernels
+  void* ftw[3] = {nullptr, nullptr, nullptr};
+  void* fmk[3] = {nullptr, nullptr, nullptr};
+  void* flam[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -296,6 +304,11 @@ void free_plan(poisfft_plan* p) {
   if (p->stage_g) cudaFree(p->stage_g);
   if (p->stage_phi) cudaFree(p->stage_phi);
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+  for (int i = 0; i < 3; i++) {
+    if (p->ftw[i]) cudaFree(p->ftw[i]);
+    if (p->fmk[i]) cudaFree(p->fmk[i]);
+    if (p->flam[i]) cudaFree(p->flam[i]);
+  }
   delete p;
 }
 
@@ -416,6 +429,138 @@ int plan_strided_sweep(poisfft_plan* p, int axis, int mode, SweepLaunch& L) {
   return POISFFT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// specialised path: every axis two-pass FP32, x periodic, y/z P, NS or DS
+// ---------------------------------------------------------------------------
+bool fast_eligible(const poisfft_plan* p) {
+  if (p->esize != 4 || p->dims < 2 || !p->r2c) return false;
+  const char* env = getenv("POISFFT_FORCE_GENERIC");
+  if (env && env[0] && env[0] != '0') return false;
+  int r1, r2, w;
+  for (int a = 0; a < p->dims; a++) {
+    if (!fast_shape(p->axes[a].n, &r1, &r2, &w)) return false;
+    const int bc = p->axes[a].bc;
+    if (a == 0 ? bc != POISFFT_P : !(bc == POISFFT_P || bc == POISFFT_NS || bc == POISFFT_DS)) return false;
+  }
+  return true;
+}
+
+bool dct_axis(const AxisPlan& ax) { return ax.bc == POISFFT_NS || ax.bc == POISFFT_DS; }
+
+// Tables of one axis for the specialised kernels, FP64 -> float:
+//   tw[s*R2 + j] = exp(-2 pi i j s / M);  mk[k] = exp(-i pi k/(2M));
+//   lam in storage order (DST-II axes: DCT-II index k holds mode M-1-k).
+int fast_upload_axis(poisfft_plan* p, int a) {
+  AxisPlan& ax = p->axes[a];
+  const int M = ax.n;
+  int R1, R2, W;
+  fast_shape(M, &R1, &R2, &W);
+  std::vector<float> tw(2 * (size_t)M), mk(2 * (size_t)M), lam(M);
+  for (int s = 0; s < R1; s++)
+    for (int j = 0; j < R2; j++) {
+      double sn, c;
+      sincos_2pi_frac((long long)j * s, M, &sn, &c);
+      tw[2 * (s * R2 + j)] = (float)c;
+      tw[2 * (s * R2 + j) + 1] = (float)-sn;
+    }
+  for (int k = 0; k < M; k++) {
+    double sn, c;
+    sincos_2pi_frac(k, 4LL * M, &sn, &c);
+    mk[2 * k] = (float)c;
+    mk[2 * k + 1] = (float)-sn;
+    lam[k] = (float)(ax.bc == POISFFT_DS ? ax.lam[M - 1 - k] : ax.lam[k]);
+  }
+  if (cudaMalloc(&p->ftw[a], tw.size() * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&p->fmk[a], mk.size() * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&p->flam[a], lam.size() * sizeof(float)) != cudaSuccess)
+    return POISFFT_ERR_ALLOC;
+  if (cudaMemcpy(p->ftw[a], tw.data(), tw.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p->fmk[a], mk.data(), mk.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p->flam[a], lam.data(), lam.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+    return POISFFT_ERR_CUDA;
+  return POISFFT_OK;
+}
+
+void plan_fast_x(poisfft_plan* p, int mode, SweepLaunch& L) {
+  memset(&L, 0, sizeof(L));
+  L.kind = 2;
+  L.M = p->nx;
+  L.fmode = mode;
+  L.axis = 0;
+  int R1, R2, W;
+  fast_shape(p->nx, &R1, &R2, &W);
+  const int rmax = std::max(R1, R2);
+  const int lpc = 256 / rmax;
+  fast::FastXArgs& a = L.fxa;
+  a.nx = p->nx;
+  a.lines = lpc;
+  a.nrows = (long long)p->ny * p->nz;
+  a.ny = p->ny;
+  a.nz = p->nz;
+  a.perm_y = p->dims >= 2 && dct_axis(p->axes[1]);
+  a.perm_z = p->dims >= 3 && dct_axis(p->axes[2]);
+  a.sign_y = p->dims >= 2 && p->axes[1].bc == POISFFT_DS;
+  a.sign_z = p->dims >= 3 && p->axes[2].bc == POISFFT_DS;
+  a.ws_ld = p->pitch;
+  const long long pairs = (a.nrows + 1) / 2;
+  L.grid = (unsigned)((pairs + lpc - 1) / lpc);
+  L.smem = (size_t)lpc * R1 * (R2 + 1) * 8;
+  const long long field = a.nrows * p->nx * 4LL;
+  L.bytes = field + a.nrows * (long long)p->ncols * 8;
+}
+
+void plan_fast_strided(poisfft_plan* p, int axis, int mode, SweepLaunch& L) {
+  memset(&L, 0, sizeof(L));
+  AxisPlan& ax = p->axes[axis];
+  const int M = ax.n;
+  int R1, R2, W;
+  fast_shape(M, &R1, &R2, &W);
+  L.kind = 3;
+  L.M = M;
+  L.fmode = mode;
+  L.fkind = dct_axis(ax) ? fast::FK_DCT : fast::FK_DFT;
+  L.axis = axis;
+  L.w = W;
+  L.box_h = std::min(M, 256);
+  L.map = axis - 1;
+  fast::FastStridedArgs& s = L.fsa;
+  double sc = 1.0;
+  for (int i = 0; i < 3; i++) sc *= p->axes[i].scale;
+  s.scale = (float)sc;
+  s.singular = p->singular;
+  s.ncols = p->ncols;
+  s.ntile_c = (p->ncols + W - 1) / W;
+  s.box_h = L.box_h;
+  s.nbox = M / L.box_h;
+  s.axis_dim = axis;
+  s.s_axis = axis == 1 ? (long long)p->pitch : (long long)p->pitch * p->ny;
+  s.s_outer = axis == 1 ? (long long)p->pitch * p->ny : (long long)p->pitch;
+  const int nouter = axis == 1 ? p->nz : p->ny;
+  L.grid = (unsigned)((long long)s.ntile_c * nouter);
+  const size_t tile_c = std::max<size_t>((size_t)R1 * (R2 * W + 8), (size_t)M * W);
+  L.smem = (tile_c * 8 + 15) / 16 * 16 + 16;
+  L.bytes = 2LL * p->ncols * (long long)p->ny * p->nz * 8;
+}
+
+void patch_fast(poisfft_plan* p) {
+  for (auto& L : p->sweeps) {
+    if (L.kind == 2) {
+      L.fxa.tw = static_cast<const float2*>(p->ftw[0]);
+      L.fxa.ws = static_cast<float2*>(p->ws);
+    } else if (L.kind == 3) {
+      const int a = L.axis;
+      fast::FastStridedArgs& s = L.fsa;
+      s.tw = static_cast<const float2*>(p->ftw[a]);
+      s.mk = static_cast<const float2*>(p->fmk[a]);
+      s.lam_in = static_cast<const float*>(p->lam[0]);
+      s.lam_ax = static_cast<const float*>(p->flam[a]);
+      s.lam_out = static_cast<const float*>(a == 1 ? (p->dims >= 3 ? p->flam[2] : p->lam[2]) : p->flam[1]);
+      s.data = static_cast<float2*>(p->ws);
+      s.err = p->err;
+    }
+  }
+}
+
 int encode_maps(poisfft_plan* p) {
   EncodeTiledFn enc = get_encode_fn();
   if (!enc) return POISFFT_ERR_CUDA;
@@ -425,12 +570,14 @@ int encode_maps(poisfft_plan* p) {
   const cuuint64_t gstride[2] = {row, row * (cuuint64_t)p->ny};
   const cuuint32_t estr[3] = {1, 1, 1};
   for (auto& L : p->sweeps) {
-    if (L.kind != 1) continue;
-    const StridedArgs& s = L.sa;
+    if (L.kind != 1 && L.kind != 3) continue;
+    const int w = L.kind == 1 ? L.sa.w : L.w;
+    const int axis_dim = L.kind == 1 ? L.sa.axis_dim : L.axis;
+    const int box_h = L.kind == 1 ? L.sa.box_h : L.box_h;
     cuuint32_t box[3];
-    box[0] = (cuuint32_t)(2 * s.w);
-    box[1] = s.axis_dim == 1 ? (cuuint32_t)s.box_h : 1u;
-    box[2] = s.axis_dim == 2 ? (cuuint32_t)s.box_h : 1u;
+    box[0] = (cuuint32_t)(2 * w);
+    box[1] = axis_dim == 1 ? (cuuint32_t)box_h : 1u;
+    box[2] = axis_dim == 2 ? (cuuint32_t)box_h : 1u;
     CUresult r = enc(&p->maps[L.map], dt, 3, p->ws, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return POISFFT_ERR_CUDA;
@@ -455,8 +602,15 @@ int enqueue(poisfft_plan* p, void* phi, const void* g, cudaStream_t st) {
       a.g = g;
       a.phi = phi;
       e = launch_x_sweep<T>(a, L.grid, L.smem, st);
-    } else {
+    } else if (L.kind == 1) {
       e = launch_strided_sweep<T>(p->maps[L.map], L.sa, L.grid, L.smem, st);
+    } else if (L.kind == 2) {
+      fast::FastXArgs a = L.fxa;
+      a.g = static_cast<const float*>(g);
+      a.phi = static_cast<float*>(phi);
+      e = launch_fast_x(L.M, L.fmode, a, L.grid, L.smem, st);
+    } else {
+      e = launch_fast_strided(L.M, L.fmode, L.fkind, p->maps[L.map], L.fsa, L.grid, L.smem, st);
     }
     if (e != cudaSuccess) return POISFFT_ERR_CUDA;
   }
@@ -540,6 +694,17 @@ int poisfft_plan_create(poisfft_plan** out, int dims, const int64_t n[], const d
   std::vector<SweepLaunch> sw;
   SweepLaunch Ls;
   int rc;
+  p->fast = fast_eligible(p);
+  if (p->fast) {
+    plan_fast_x(p, fast::FM_FWD, Ls);
+    sw.push_back(Ls);
+    if (dims == 3) { plan_fast_strided(p, 1, fast::FM_FWD, Ls); sw.push_back(Ls); }
+    plan_fast_strided(p, dims == 3 ? 2 : 1, fast::FM_FUSED, Ls);
+    sw.push_back(Ls);
+    if (dims == 3) { plan_fast_strided(p, 1, fast::FM_INV, Ls); sw.push_back(Ls); }
+    plan_fast_x(p, fast::FM_INV, Ls);
+    sw.push_back(Ls);
+  } else {
   if ((rc = plan_x_sweep(p, 0, Ls)) != POISFFT_OK) { free_plan(p); return rc; }
   sw.push_back(Ls);
   const int fused_axis = dims == 3 ? 2 : 1;
@@ -555,6 +720,7 @@ int poisfft_plan_create(poisfft_plan** out, int dims, const int64_t n[], const d
   }
   if ((rc = plan_x_sweep(p, 1, Ls)) != POISFFT_OK) { free_plan(p); return rc; }
   sw.push_back(Ls);
+  }
   p->sweeps = sw;
 
   // device resources
@@ -563,7 +729,9 @@ int poisfft_plan_create(poisfft_plan** out, int dims, const int64_t n[], const d
   if (cudaMalloc(&p->ws, p->ws_bytes) != cudaSuccess) { cudaGetLastError(); free_plan(p); return POISFFT_ERR_ALLOC; }
   if (cudaMemset(p->ws, 0, p->ws_bytes) != cudaSuccess) { free_plan(p); return POISFFT_ERR_CUDA; }
   rc = p->esize == 4 ? upload_tables<float>(p) : upload_tables<double>(p);
+  for (int a = 0; p->fast && a < dims && rc == POISFFT_OK; a++) rc = fast_upload_axis(p, a);
   if (rc != POISFFT_OK) { cudaGetLastError(); free_plan(p); return rc; }
+  if (p->fast) patch_fast(p);
   // the sweeps were planned before the buffers existed: patch the pointers
   for (auto& L : p->sweeps) {
     if (L.kind == 0) {
@@ -571,7 +739,7 @@ int poisfft_plan_create(poisfft_plan** out, int dims, const int64_t n[], const d
       L.xa.perm = p->perm[0];
       L.xa.ws = p->ws;
       L.xa.err = p->err;
-    } else {
+    } else if (L.kind == 1) {
       const int a = L.sa.axis_dim;
       L.sa.tables = p->tables[a];
       L.sa.perm = p->perm[a];
@@ -665,9 +833,14 @@ int poisfft_launch_info(const poisfft_plan* p, int i, int64_t out[4]) {
   if (!p || !out || i < 0 || i >= (int)p->sweeps.size()) return POISFFT_ERR_INVALID_ARG;
   const SweepLaunch& L = p->sweeps[i];
   out[0] = L.bytes;
-  out[1] = L.kind;
-  out[2] = L.kind == 0 ? L.xa.mode : L.sa.mode;
-  out[3] = L.kind == 0 ? 0 : L.sa.axis_dim;
+  out[1] = (L.kind == 0 || L.kind == 2) ? 0 : 1;
+  if (L.kind >= 2) {
+    out[2] = L.fmode;
+    out[3] = L.axis;
+  } else {
+    out[2] = L.kind == 0 ? L.xa.mode : L.sa.mode;
+    out[3] = L.kind == 0 ? 0 : L.sa.axis_dim;
+  }
   return POISFFT_OK;
 }
 

@@ -218,3 +218,40 @@ def test_misaligned_pointer_rejected(pb):
         buf = torch.zeros(8 * 8 * 8 + 1, device="cuda")
         rc = pb.solve(plan.handle, buf.data_ptr() + 2, buf.data_ptr(), None)
         assert rc == pb.ERR_MISALIGNED
+
+
+# ---------------------------------------------------------------------------
+# specialised two-pass kernels (x periodic, y/z in {P, NS, DS}, lengths
+# 64...1024) and the generic kernels on the same shapes
+# ---------------------------------------------------------------------------
+
+FAST3 = [(64, 64, 64), (128, 64, 256), (1024, 64, 64), (512, 256, 64), (64, 128, 1024), (256, 1024, 64)]
+FAST_BCS = [(W.P, W.P, W.P), (W.P, W.P, W.NS), (W.P, W.DS, W.NS), (W.P, W.NS, W.DS), (W.P, W.DS, W.P),
+            (W.P, W.NS, W.NS)]
+
+
+@pytest.mark.parametrize("n", FAST3, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("bcs", FAST_BCS, ids=lambda b: "".join(O.BC_NAMES[x] for x in b))
+def test_fast_path_3d(pb, n, bcs):
+    shape = tuple(reversed(n))
+    method = "dense" if np.prod(n) <= 1 << 20 else "fft"
+    check(pb, shape, bcs, W.FD2, "f32", seed=12, method=method)
+
+
+@pytest.mark.parametrize("n,bcs", [((1024, 512), (W.P, W.NS)), ((64, 1024), (W.P, W.DS)),
+                                   ((256, 256), (W.P, W.P)), ((128, 64), (W.P, W.NS))])
+def test_fast_path_2d(pb, n, bcs):
+    check(pb, tuple(reversed(n)), bcs, W.SPECTRAL, "f32", seed=13, method="fft")
+
+
+def test_fast_and_generic_kernels_agree(pb, monkeypatch):
+    shape = (128, 64, 256)
+    bcs, Ls = (W.P, W.DS, W.NS), (1.0, 1.0, 1.0)
+    g = W.normal(shape, 14, dtype=np.float32)
+    fast = gpu_solve(pb, g, bcs, Ls, W.FD2, "f32")
+    monkeypatch.setenv("POISFFT_FORCE_GENERIC", "1")
+    generic = gpu_solve(pb, g, bcs, Ls, W.FD2, "f32")
+    ref = O.solve(g.astype(np.float64), bcs, Ls, W.FD2, method="fft")
+    assert O.rel_max_error(fast, ref) < 1e-5
+    assert O.rel_max_error(generic, ref) < 1e-5
+    assert O.rel_max_error(fast, generic) < 2e-5
