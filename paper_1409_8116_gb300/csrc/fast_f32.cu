@@ -11,6 +11,8 @@ cudaError_t run_strided(const CUtensorMap& map, const fast::FastStridedArgs& a, 
                         cudaStream_t s) {
   auto k = fast::fast_strided_kernel<R1, R2, W, MODE, KIND>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   k<<<grid, W * fast::Shape<R1, R2>::RMAX, smem, s>>>(map, a);
   return cudaGetLastError();
@@ -34,6 +36,8 @@ template <int R1, int R2, int MODE>
 cudaError_t run_x(const fast::FastXArgs& a, unsigned grid, size_t smem, cudaStream_t s) {
   auto k = fast::fast_x_kernel<R1, R2, MODE>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   k<<<grid, 256, smem, s>>>(a);
   return cudaGetLastError();

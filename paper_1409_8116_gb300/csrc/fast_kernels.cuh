@@ -38,6 +38,7 @@ enum FastMode : int { FM_FWD = 0, FM_INV = 1, FM_FUSED = 2 };
 struct FastStridedArgs {
   const float2* tw;        // tw[s * R2 + j] = exp(-2 pi i j s / M), s < R1, j < R2
   const float2* mk;        // exp(-i pi k / (2M)), k < M (DCT axes)
+  const float4* pk;        // fused DCT axes: (lam_ax[k], lam_ax[(M-k) mod M], cos(pi k/M), sin(pi k/M))
   const float* lam_in;     // x eigenvalues by column
   const float* lam_ax;     // swept-axis eigenvalues in storage order
   const float* lam_out;    // outer-axis eigenvalues in storage order
@@ -81,8 +82,12 @@ struct Shape {
 // Tile: W columns x M rows.  Thread t: column c = t % W, butterfly index
 // t / W.  Smem: TMA layout row*W + c, then padded layout
 // block*(R2*W + 8) + row*W + c.
+// Resident CTAs per SM: 3 for the single-transform sweeps; the fused sweep
+// keeps 2 (its register demand would spill at 3).
+template <int MODE> struct StridedMinBlocks { static constexpr int value = MODE == 2 ? 2 : 3; };
+
 template <int R1, int R2, int W, int MODE, int KIND>
-__global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, 2)
+__global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, StridedMinBlocks<MODE>::value)
     fast_strided_kernel(const __grid_constant__ CUtensorMap tmap, const FastStridedArgs a) {
   constexpr int M = R1 * R2;
   constexpr int NT = W * Shape<R1, R2>::RMAX;
@@ -195,23 +200,20 @@ __global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, 2)
           if (zero_row && k == 0) f = 0.f;
           y[s2] = make_float2(y[s2].x * f, y[s2].y * f);
         } else {
-          // X_k, X_{M-k} from Y_k, Y_{M-k}; scale both; V_k = conj(w_k) (X'_k - i X'_{M-k})
-          const int kp = k == 0 ? 0 : M - k;
-          const float2 yk = y[s2];
-          const float2 yp = sm[(kp % R1) * BS + (kp / R1) * W + c];
-          const float2 w = __ldg(&a.mk[k]);
-          const float2 wy = cmul<float>(w, yk);
-          const float2 cy = cmulc<float>(yp, w);
-          const float2 xk = cadd<float>(wy, cy);
-          float fk = __fdividef(a.scale, lam_xo + __ldg(&a.lam_ax[k]));
+          // DCT-II post, divide and DCT-III pre in one step: with
+          // X_k = w Y_k + conj(w) Y_{M-k}, X_{M-k} = i (w Y_k - conj(w) Y_{M-k}),
+          // V_k = conj(w) (f_k X_k - i f_{M-k} X_{M-k})
+          //     = (f_k + f_{M-k}) Y_k + (f_k - f_{M-k}) conj(w)^2 Y_{M-k};  k = 0: 2 f_0 Y_0
+          // partner M-k: block (R1-b) mod R1, row R2-1-s2 (b > 0) or (R2-s2) mod R2 (b = 0)
+          const int prow = b == 0 ? (R2 - s2) % R2 : R2 - 1 - s2;
+          const float2 yp = sm[((R1 - b) % R1) * BS + prow * W + c];
+          const float4 t = __ldg(&a.pk[k]);
+          float fk = __fdividef(a.scale, lam_xo + t.x);
           if (zero_row && k == 0) fk = 0.f;
-          float2 v = make_float2(xk.x * fk, xk.y * fk);
-          if (k != 0) {
-            const float2 xm = mul_i<float>(csub<float>(wy, cy));  // X_{M-k} = i (w Y_k - conj(w) Y_{M-k})
-            const float fm = __fdividef(a.scale, lam_xo + __ldg(&a.lam_ax[kp]));
-            v = make_float2(v.x + xm.y * fm, v.y - xm.x * fm);     // X'_k - i X'_{M-k}
-          }
-          y[s2] = cmulc<float>(v, w);
+          const float fm = k == 0 ? fk : __fdividef(a.scale, lam_xo + t.y);
+          const float2 cyp = make_float2(t.z * yp.x - t.w * yp.y, t.z * yp.y + t.w * yp.x);
+          const float al = fk + fm, be = fk - fm;
+          y[s2] = make_float2(al * y[s2].x + be * cyp.x, al * y[s2].y + be * cyp.y);
         }
       }
       Dft<float, R2, true>::run(y);
@@ -289,7 +291,7 @@ __device__ __forceinline__ void ws_row_of(const FastXArgs& a, long long r, long 
 }
 
 template <int R1, int R2, int MODE>
-__global__ void __launch_bounds__(256, 2) fast_x_kernel(const FastXArgs a) {
+__global__ void __launch_bounds__(256, MODE == 0 ? 2 : 3) fast_x_kernel(const FastXArgs a) {
   constexpr int M = R1 * R2;
   constexpr int RMAX = Shape<R1, R2>::RMAX;
   constexpr int LS = R1 * (R2 + 1);  // padded line stride (complex)
@@ -349,15 +351,24 @@ __global__ void __launch_bounds__(256, 2) fast_x_kernel(const FastXArgs a) {
       if (vb) db[k] = make_float2(sb * B.x, sb * B.y);
     }
   } else {
-    // C2R assembly into the digit-reversed arrangement
+    // C2R assembly into the digit-reversed arrangement (all loads first)
     constexpr int NH = M / 2 + 1;
+    constexpr int NK = (NH + RMAX - 1) / RMAX;
     const float2* sa_p = a.ws + wa * a.ws_ld;
     const float2* sb_p = a.ws + wb * a.ws_ld;
-    for (int k = bi; k < NH; k += RMAX) {
-      float2 A = va ? sa_p[k] : make_float2(0.f, 0.f);
-      float2 B = vb ? sb_p[k] : make_float2(0.f, 0.f);
-      A = make_float2(sa * A.x, sa * A.y);
-      B = make_float2(sb * B.x, sb * B.y);
+    float2 Av[NK], Bv[NK];
+#pragma unroll
+    for (int i = 0; i < NK; i++) {
+      const int k = bi + i * RMAX;
+      Av[i] = (va && k < NH) ? sa_p[k] : make_float2(0.f, 0.f);
+      Bv[i] = (vb && k < NH) ? sb_p[k] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < NK; i++) {
+      const int k = bi + i * RMAX;
+      if (k >= NH) break;
+      const float2 A = make_float2(sa * Av[i].x, sa * Av[i].y);
+      const float2 B = make_float2(sb * Bv[i].x, sb * Bv[i].y);
       if (k == 0 || 2 * k == M) {
         line[xpos<R1, R2>(k)] = make_float2(A.x, B.x);
       } else {

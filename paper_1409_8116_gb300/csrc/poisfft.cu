@@ -287,6 +287,7 @@ struct poisfft_plan {
   bool fast = false;                 // specialised two-pass FP32 kernels
   void* ftw[3] = {nullptr, nullptr, nullptr};
   void* fmk[3] = {nullptr, nullptr, nullptr};
+  void* fpk[3] = {nullptr, nullptr, nullptr};
   void* flam[3] = {nullptr, nullptr, nullptr};
 };
 
@@ -307,6 +308,7 @@ void free_plan(poisfft_plan* p) {
   for (int i = 0; i < 3; i++) {
     if (p->ftw[i]) cudaFree(p->ftw[i]);
     if (p->fmk[i]) cudaFree(p->fmk[i]);
+    if (p->fpk[i]) cudaFree(p->fpk[i]);
     if (p->flam[i]) cudaFree(p->flam[i]);
   }
   delete p;
@@ -449,13 +451,14 @@ bool dct_axis(const AxisPlan& ax) { return ax.bc == POISFFT_NS || ax.bc == POISF
 
 // Tables of one axis for the specialised kernels, FP64 -> float:
 //   tw[s*R2 + j] = exp(-2 pi i j s / M);  mk[k] = exp(-i pi k/(2M));
+//   pk[k] = (lam[k], lam[(M-k) mod M], cos(pi k/M), sin(pi k/M));
 //   lam in storage order (DST-II axes: DCT-II index k holds mode M-1-k).
 int fast_upload_axis(poisfft_plan* p, int a) {
   AxisPlan& ax = p->axes[a];
   const int M = ax.n;
   int R1, R2, W;
   fast_shape(M, &R1, &R2, &W);
-  std::vector<float> tw(2 * (size_t)M), mk(2 * (size_t)M), lam(M);
+  std::vector<float> tw(2 * (size_t)M), mk(2 * (size_t)M), pk(4 * (size_t)M), lam(M);
   for (int s = 0; s < R1; s++)
     for (int j = 0; j < R2; j++) {
       double sn, c;
@@ -468,14 +471,23 @@ int fast_upload_axis(poisfft_plan* p, int a) {
     sincos_2pi_frac(k, 4LL * M, &sn, &c);
     mk[2 * k] = (float)c;
     mk[2 * k + 1] = (float)-sn;
+    sincos_2pi_frac(k, 2LL * M, &sn, &c);  // exp(+i pi k / M)
+    pk[4 * k + 2] = (float)c;
+    pk[4 * k + 3] = (float)sn;
     lam[k] = (float)(ax.bc == POISFFT_DS ? ax.lam[M - 1 - k] : ax.lam[k]);
+  }
+  for (int k = 0; k < M; k++) {
+    pk[4 * k] = lam[k];
+    pk[4 * k + 1] = lam[k == 0 ? 0 : M - k];
   }
   if (cudaMalloc(&p->ftw[a], tw.size() * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&p->fmk[a], mk.size() * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&p->fpk[a], pk.size() * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&p->flam[a], lam.size() * sizeof(float)) != cudaSuccess)
     return POISFFT_ERR_ALLOC;
   if (cudaMemcpy(p->ftw[a], tw.data(), tw.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(p->fmk[a], mk.data(), mk.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(p->fpk[a], pk.data(), pk.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(p->flam[a], lam.data(), lam.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
     return POISFFT_ERR_CUDA;
   return POISFFT_OK;
@@ -552,6 +564,7 @@ void patch_fast(poisfft_plan* p) {
       fast::FastStridedArgs& s = L.fsa;
       s.tw = static_cast<const float2*>(p->ftw[a]);
       s.mk = static_cast<const float2*>(p->fmk[a]);
+      s.pk = static_cast<const float4*>(p->fpk[a]);
       s.lam_in = static_cast<const float*>(p->lam[0]);
       s.lam_ax = static_cast<const float*>(p->flam[a]);
       s.lam_out = static_cast<const float*>(a == 1 ? (p->dims >= 3 ? p->flam[2] : p->lam[2]) : p->flam[1]);

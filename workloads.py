@@ -104,6 +104,11 @@ WORKLOADS = {
     "ppn_fd2_512_f32": dict(
         n=(512, 512, 512), bcs=(P, P, NS), Ls=(1.0, 1.0, 1.0), approx=FD2,
         dtype="f32", gen=("normal_meanfree", 3)),
+    # 256 x 256 x 1024: the 1024-point z sweeps of the 1024^3 workload on a
+    # field small enough for full profiler captures
+    "ppn_fd2_256x256x1024_f32": dict(
+        n=(256, 256, 1024), bcs=(P, P, NS), Ls=(1.0, 1.0, 4.0), approx=FD2,
+        dtype="f32", gen=("normal_meanfree", 3)),
     # 1024^3 FP32 FD2, periodic x,y, staggered Neumann z, L = 1 per axis
     "ppn_fd2_1024_f32": dict(
         n=(1024, 1024, 1024), bcs=(P, P, NS), Ls=(1.0, 1.0, 1.0), approx=FD2,
