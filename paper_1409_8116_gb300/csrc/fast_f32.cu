@@ -50,25 +50,26 @@ cudaError_t run_x_m(int mode, const fast::FastXArgs& a, unsigned grid, size_t sm
 
 }  // namespace
 
+// Tile widths measured on GB300 (W = 4 and 16 were slower for these sizes).
 bool fast_shape(int M, int* R1, int* R2, int* W) {
   switch (M) {
     case 64: *R1 = 8; *R2 = 8; *W = 32; return true;
     case 128: *R1 = 16; *R2 = 8; *W = 16; return true;
-    case 256: *R1 = 16; *R2 = 16; *W = 16; return true;
+    case 256: *R1 = 16; *R2 = 16; *W = 8; return true;
     case 512: *R1 = 32; *R2 = 16; *W = 8; return true;
     case 1024: *R1 = 32; *R2 = 32; *W = 8; return true;
     default: return false;
   }
 }
 
-cudaError_t launch_fast_strided(int M, int mode, int kind, const CUtensorMap& map, const fast::FastStridedArgs& a,
-                                unsigned grid, size_t smem, cudaStream_t s) {
-  switch (M) {
-    case 64: return run_strided_mk<8, 8, 32>(mode, kind, map, a, grid, smem, s);
-    case 128: return run_strided_mk<16, 8, 16>(mode, kind, map, a, grid, smem, s);
-    case 256: return run_strided_mk<16, 16, 16>(mode, kind, map, a, grid, smem, s);
-    case 512: return run_strided_mk<32, 16, 8>(mode, kind, map, a, grid, smem, s);
-    case 1024: return run_strided_mk<32, 32, 8>(mode, kind, map, a, grid, smem, s);
+cudaError_t launch_fast_strided(int M, int W, int mode, int kind, const CUtensorMap& map,
+                                const fast::FastStridedArgs& a, unsigned grid, size_t smem, cudaStream_t s) {
+  switch (M * 64 + W) {
+    case 64 * 64 + 32: return run_strided_mk<8, 8, 32>(mode, kind, map, a, grid, smem, s);
+    case 128 * 64 + 16: return run_strided_mk<16, 8, 16>(mode, kind, map, a, grid, smem, s);
+    case 256 * 64 + 8: return run_strided_mk<16, 16, 8>(mode, kind, map, a, grid, smem, s);
+    case 512 * 64 + 8: return run_strided_mk<32, 16, 8>(mode, kind, map, a, grid, smem, s);
+    case 1024 * 64 + 8: return run_strided_mk<32, 32, 8>(mode, kind, map, a, grid, smem, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -9,8 +9,9 @@
 //     the DFT coefficient k = b + R1*s2 (digit-reversed arrangement).
 //   DIT pass A (radix R2) consumes that arrangement block by block, DIT pass B
 //     (radix R1, twiddle before the butterfly) returns natural order.
-// After pass 1 the tile sits in a padded layout (64 bytes after every block
-// of R2 rows) so that pass 2 reads whole blocks without bank conflicts.
+// After pass 1 the tile sits in a padded layout (min(W, 8) complex after
+// every block of R2 rows) so that pass 2 reads whole blocks without bank
+// conflicts.
 //
 // Axes with DCT-II / DCT-III (Neumann staggered) and DST-II / DST-III
 // (Dirichlet staggered) use the even/odd reordering of Makhoul (1980): the
@@ -81,17 +82,22 @@ struct Shape {
 // ---------------------------------------------------------------------------
 // Tile: W columns x M rows.  Thread t: column c = t % W, butterfly index
 // t / W.  Smem: TMA layout row*W + c, then padded layout
-// block*(R2*W + 8) + row*W + c.
-// Resident CTAs per SM: 3 for the single-transform sweeps; the fused sweep
-// keeps 2 (its register demand would spill at 3).
-template <int MODE> struct StridedMinBlocks { static constexpr int value = MODE == 2 ? 2 : 3; };
+// block*(R2*W + pad) + row*W + c.
+// Resident CTAs per SM (register budget): 768 threads for the single-
+// transform sweeps, 512 for the fused sweep (its registers would spill).
+template <int MODE, int NT> struct StridedMinBlocks {
+  static constexpr int value = (MODE == 2 ? 512 : 768) / NT;
+};
+// Padding after every block of R2 rows in the padded layout (complex):
+// shifts consecutive blocks across the smem banks for narrow tiles.
+template <int W> struct BlockPad { static constexpr int value = W < 8 ? W : 8; };
 
 template <int R1, int R2, int W, int MODE, int KIND>
-__global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, StridedMinBlocks<MODE>::value)
+__global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, StridedMinBlocks<MODE, W * Shape<R1, R2>::RMAX>::value)
     fast_strided_kernel(const __grid_constant__ CUtensorMap tmap, const FastStridedArgs a) {
   constexpr int M = R1 * R2;
   constexpr int NT = W * Shape<R1, R2>::RMAX;
-  constexpr int BS = R2 * W + 8;  // padded block stride (complex)
+  constexpr int BS = R2 * W + BlockPad<W>::value;  // padded block stride (complex)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
   constexpr int TILE_C = (R1 * BS > M * W) ? R1 * BS : M * W;

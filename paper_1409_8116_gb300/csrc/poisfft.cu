@@ -549,7 +549,7 @@ void plan_fast_strided(poisfft_plan* p, int axis, int mode, SweepLaunch& L) {
   s.s_outer = axis == 1 ? (long long)p->pitch * p->ny : (long long)p->pitch;
   const int nouter = axis == 1 ? p->nz : p->ny;
   L.grid = (unsigned)((long long)s.ntile_c * nouter);
-  const size_t tile_c = std::max<size_t>((size_t)R1 * (R2 * W + 8), (size_t)M * W);
+  const size_t tile_c = std::max<size_t>((size_t)R1 * (R2 * W + std::min(W, 8)), (size_t)M * W);
   L.smem = (tile_c * 8 + 15) / 16 * 16 + 16;
   L.bytes = 2LL * p->ncols * (long long)p->ny * p->nz * 8;
 }
@@ -623,7 +623,7 @@ int enqueue(poisfft_plan* p, void* phi, const void* g, cudaStream_t st) {
       a.phi = static_cast<float*>(phi);
       e = launch_fast_x(L.M, L.fmode, a, L.grid, L.smem, st);
     } else {
-      e = launch_fast_strided(L.M, L.fmode, L.fkind, p->maps[L.map], L.fsa, L.grid, L.smem, st);
+      e = launch_fast_strided(L.M, L.w, L.fmode, L.fkind, p->maps[L.map], L.fsa, L.grid, L.smem, st);
     }
     if (e != cudaSuccess) return POISFFT_ERR_CUDA;
   }
