@@ -48,16 +48,36 @@ UNIT = "grid-pts/s"
 DEFAULT_WORKLOAD = "ppn_fd2_1024_f32"
 BC_NAME = {0: "P", 1: "DR", 2: "DS", 3: "NR", 4: "NS"}
 
+# DRAM traffic / algorithmic bytes of the specialised strided launches, from
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) on the
+# 512x512x1024 workload (profiles/traffic_fast_strided_512x512x1024.md).
+# Valid only while the kernel sources hash to TRAFFIC_SRC_SHA256.
+TRAFFIC_RATIO = {("strided_sweep", "fused"): 0.980, ("strided_sweep", "forward"): 0.979,
+                 ("strided_sweep", "backward"): 0.984}
+TRAFFIC_SRC_SHA256 = "210343074b2518ba7a24450bdfd0d6d23e57e8fc3110e8bd237da6fc7ade705f"
+TRAFFIC_SOURCES = ["fast_kernels.cuh", "fft_engine.cuh", "fast_f32.cu"]
+
+
+def kernel_source_sha256():
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_1409_8116_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(W.WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 error check of the solution")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer (e2e) measurement")
     return ap.parse_args()
 
 
@@ -66,6 +86,24 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", str(rank)))
     return rank, world, local
+
+
+def reduce_max(x: float, world: int, device: str = "cpu") -> float:
+    """Max of a per-rank scalar over all ranks (the step time of the slowest
+    rank); identity for one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(points_per_rank: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job grid points per second: every rank solves its own replica."""
+    return world * points_per_rank * steps / seconds
 
 
 def load_peaks():
@@ -262,13 +300,8 @@ def run_ours(args):
     ms_total = e0.elapsed_time(e1)
     per_launch_ms, nsolves = plan.profile_read()
     assert plan.check(stream) == pb.OK
-    t_local = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms_max = float(t_local.item())
-    value = world * npts * args.steps / (ms_max / 1e3)
+    ms_max = reduce_max(ms_total, world, "cuda")
+    value = throughput(npts, args.steps, world, ms_max / 1e3)
 
     # dominant launch: largest share of the step time
     shares = [t / sum(per_launch_ms) for t in per_launch_ms]
@@ -276,28 +309,30 @@ def run_ours(args):
     dom_ms = per_launch_ms[dom] / nsolves
     peak, peak_kind = load_peaks()
     achieved = launches[dom]["bytes"] / (dom_ms / 1e3) / 1e9
+    key = (launches[dom]["kernel"], launches[dom]["mode"])
+    traffic = None
+    if key in TRAFFIC_RATIO and kernel_source_sha256() == TRAFFIC_SRC_SHA256:
+        traffic = TRAFFIC_RATIO[key] * launches[dom]["bytes"]
     per_launch = [dict(launches[i], ms=per_launch_ms[i] / nsolves, share=shares[i],
                        gbs=launches[i]["bytes"] / (per_launch_ms[i] / nsolves / 1e3) / 1e9)
                   for i in range(len(launches))]
     step_bytes = sum(l["bytes"] for l in launches)
 
     # ---- end to end through the host-buffer entry point
-    gh = torch.from_numpy(g_host).pin_memory()
-    ph = torch.empty_like(gh).pin_memory()
-    for _ in range(max(1, args.warmup)):
-        plan.solve_host(ph, gh, stream)
-    e2e_steps = max(1, min(args.steps, 5))
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        plan.solve_host(ph, gh, stream)
-    t_e2e = time.perf_counter() - t0
-    t_e2e_t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.all_reduce(t_e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * npts * e2e_steps / float(t_e2e_t.item())
+    e2e_value = None
+    if not args.no_e2e:
+        gh = torch.from_numpy(g_host).pin_memory()
+        ph = torch.empty_like(gh).pin_memory()
+        for _ in range(max(1, args.warmup)):
+            plan.solve_host(ph, gh, stream)
+        e2e_steps = max(1, min(args.steps, 5))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            plan.solve_host(ph, gh, stream)
+        t_e2e = reduce_max(time.perf_counter() - t0, world, "cuda")
+        e2e_value = throughput(npts, e2e_steps, world, t_e2e)
+        del gh, ph
 
     # ---- accuracy against the FP64 oracle (not timed)
     err = None
@@ -306,8 +341,10 @@ def run_ours(args):
 
         ref = O.solve(g_host.astype(np.float64), spec["bcs"], spec["Ls"], spec["approx"],
                       method="dense" if npts <= 64 ** 3 else "fft")
+        t_chk = time.perf_counter()
         err = O.rel_max_error(phi.cpu().numpy().astype(np.float64), ref)
         del ref
+        print(f"# FP64 check {time.perf_counter() - t_chk:.1f} s", file=sys.stderr)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -322,13 +359,14 @@ def run_ours(args):
             "max_rel_err_vs_fp64": err,
             "hbm_frac_step": step_bytes * args.steps / (ms_max / 1e3) / 1e9 / peak,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic,
                          "kernel": f"{launches[dom]['kernel']} ({launches[dom]['mode']}, axis {launches[dom]['axis']})",
                          "peak_source": f"{peak_kind} hbm_gbs"},
             "launches": per_launch,
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": npts * esize,
-                    "d2h_bytes_per_step": npts * esize},
+            "e2e": None if e2e_value is None else {
+                "value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": npts * esize,
+                "d2h_bytes_per_step": npts * esize},
             "gpu_launches": len(launches) * args.steps,
             "clocks": clocks,
         }

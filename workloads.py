@@ -109,6 +109,11 @@ WORKLOADS = {
     "ppn_fd2_256x256x1024_f32": dict(
         n=(256, 256, 1024), bcs=(P, P, NS), Ls=(1.0, 1.0, 4.0), approx=FD2,
         dtype="f32", gen=("normal_meanfree", 3)),
+    # 512 x 512 x 1024: profiling case of the 1024-point z kernels with a
+    # field (1 GiB) far larger than L2
+    "ppn_fd2_512x512x1024_f32": dict(
+        n=(512, 512, 1024), bcs=(P, P, NS), Ls=(1.0, 1.0, 2.0), approx=FD2,
+        dtype="f32", gen=("normal_meanfree", 3)),
     # 1024^3 FP32 FD2, periodic x,y, staggered Neumann z, L = 1 per axis
     "ppn_fd2_1024_f32": dict(
         n=(1024, 1024, 1024), bcs=(P, P, NS), Ls=(1.0, 1.0, 1.0), approx=FD2,
