@@ -53,7 +53,7 @@ enum {
   POISFFT_ERR_CUDA = -5,            /* a CUDA runtime/driver call failed (no device, launch error, ...) */
   POISFFT_ERR_MISALIGNED = -6,      /* phi or g not aligned to the element size */
   POISFFT_ERR_TIMEOUT = -7,         /* a bounded device wait gave up (error flag set by a kernel) */
-  POISFFT_ERR_NOT_IMPLEMENTED = -8  /* valid arguments outside what this build implements */
+  POISFFT_ERR_NOT_IMPLEMENTED = -8  /* valid arguments outside what this entry point implements */
 };
 
 typedef struct poisfft_plan poisfft_plan;  /* opaque; owned by the library */
@@ -141,6 +141,8 @@ int poisfft_plan_info(const poisfft_plan* plan, int64_t info[4]);
  *     (other streams, other host threads) race on the array: serialise them.
  *   - Tables are copied from pageable host memory, so the call waits for
  *     the work already queued on `stream` before it returns.
+ * x non-periodic together with a periodic y or z returns
+ * POISFFT_ERR_NOT_IMPLEMENTED here (poisfft_solve handles it).
  * Returns the status codes of poisfft_plan_create / poisfft_solve; check
  * the kernels' bounded waits with cudaStreamSynchronize (no plan exists
  * for poisfft_check). */
@@ -161,7 +163,8 @@ int poisfft_profile_read(poisfft_plan* plan, double* ms, int cap, int* nlaunch, 
 
 /* Description of launch position i of a solve (host only).
  *   out[0] = algorithmic HBM bytes of the launch (reads + writes of its data)
- *   out[1] = kernel: 0 contiguous (x) sweep, 1 strided (y/z) sweep
+ *   out[1] = kernel: 0 contiguous (x) sweep, 1 strided (y/z) sweep,
+ *            2 separate eigenvalue divide (x non-periodic with periodic y/z)
  *   out[2] = mode: 0 forward, 1 backward, 2 forward + divide + backward
  *   out[3] = axis: 0 x, 1 y, 2 z
  * Returns POISFFT_OK or POISFFT_ERR_INVALID_ARG (i out of range). */

@@ -207,7 +207,7 @@ class Plan:
             rc = lib.poisfft_launch_info(self._p, i, v)
             if rc != OK:
                 raise PoisFFTError(rc, "poisfft_launch_info")
-            out.append(dict(bytes=v[0], kernel=("x_sweep", "strided_sweep")[v[1]],
+            out.append(dict(bytes=v[0], kernel=("x_sweep", "strided_sweep", "pair_divide")[v[1]],
                             mode=("forward", "backward", "fused")[v[2]], axis="xyz"[v[3]]))
         return out
 

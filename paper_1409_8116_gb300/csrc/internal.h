@@ -103,4 +103,22 @@ struct StridedArgs {
   int* err;
 };
 
+// Eigenvalue divide over the whole spectrum when x is not periodic but y or
+// z is: every complex workspace element carries two real x columns
+// (kx = 2c real part, 2c + 1 imaginary part) whose y/z DFTs are mixed.  The
+// element at k = (c, ky, kz) and its mirror -k (negated along periodic axes)
+// give A(k) = (Z(k) + conj Z(-k))/2 and B(k) = (Z(k) - conj Z(-k))/(2i),
+// the spectra of the two columns, which are divided separately.
+struct PairDivideArgs {
+  void* data;             // workspace [nz][ny][pitch] complex
+  long long pitch;
+  int ncols, nx, ny, nz;
+  int per_y, per_z;       // axis is periodic (mirror index (n - k) mod n)
+  const void* lam_x;      // kx = 0..nx-1
+  const void* lam_y;
+  const void* lam_z;
+  double scale;
+  int singular;
+};
+
 }  // namespace pf

@@ -22,6 +22,9 @@ template <typename T>
 cudaError_t launch_strided_sweep(const CUtensorMap& map, const StridedArgs& a, unsigned grid, size_t smem,
                                  cudaStream_t s);
 
+template <typename T>
+cudaError_t launch_pair_divide(const PairDivideArgs& a, cudaStream_t s);
+
 // Specialised FP32 two-pass kernels (fast_f32.cu) for line lengths M in
 // {64, 128, 256, 512, 1024}: radices R1 x R2 and the tile width W.
 bool fast_shape(int M, int* R1, int* R2, int* W);

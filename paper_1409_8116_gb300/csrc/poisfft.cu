@@ -214,11 +214,12 @@ int build_axis(AxisPlan& ax, int bc, int n, double L, int approx, int emax, bool
 }
 
 struct SweepLaunch {
-  int kind;               // 0 x sweep, 1 strided sweep, 2 fast x sweep, 3 fast strided sweep
+  int kind;               // 0 x sweep, 1 strided sweep, 2 fast x sweep, 3 fast strided sweep, 4 pair divide
   XArgs xa;
   StridedArgs sa;
   fast::FastXArgs fxa;
   fast::FastStridedArgs fsa;
+  PairDivideArgs pda;
   int M, fmode, fkind, axis, w, box_h;  // fast sweeps
   int map;                // tensor map index (strided)
   unsigned grid;
@@ -617,6 +618,8 @@ int enqueue(poisfft_plan* p, void* phi, const void* g, cudaStream_t st) {
       e = launch_x_sweep<T>(a, L.grid, L.smem, st);
     } else if (L.kind == 1) {
       e = launch_strided_sweep<T>(p->maps[L.map], L.sa, L.grid, L.smem, st);
+    } else if (L.kind == 4) {
+      e = launch_pair_divide<T>(L.pda, st);
     } else if (L.kind == 2) {
       fast::FastXArgs a = L.fxa;
       a.g = static_cast<const float*>(g);
@@ -672,12 +675,12 @@ int poisfft_plan_create(poisfft_plan** out, int dims, const int64_t n[], const d
     LL[a] = L[a];
   }
   if ((double)nn[0] * nn[1] * nn[2] > 4.0e10) return POISFFT_ERR_UNSUPPORTED_SIZE;
-  // x periodic -> half-spectrum workspace; no periodic axis -> real workspace.
-  // x non-periodic with a periodic y or z is a valid problem outside this build.
+  // x periodic -> half-spectrum workspace; otherwise the real transformed
+  // field viewed as complex pairs.  x non-periodic with a periodic y or z
+  // divides in a separate pass that pairs k with -k (PairDivideArgs).
   const bool xper = bca[0] == POISFFT_P;
   bool any_per_yz = false;
   for (int a = 1; a < dims; a++) any_per_yz |= bca[a] == POISFFT_P;
-  if (!xper && any_per_yz) return POISFFT_ERR_NOT_IMPLEMENTED;
 
   poisfft_plan* p = new (std::nothrow) poisfft_plan();
   if (!p) return POISFFT_ERR_ALLOC;
@@ -717,6 +720,35 @@ int poisfft_plan_create(poisfft_plan** out, int dims, const int64_t n[], const d
     if (dims == 3) { plan_fast_strided(p, 1, fast::FM_INV, Ls); sw.push_back(Ls); }
     plan_fast_x(p, fast::FM_INV, Ls);
     sw.push_back(Ls);
+  } else if (!xper && any_per_yz) {
+    if ((rc = plan_x_sweep(p, 0, Ls)) != POISFFT_OK) { free_plan(p); return rc; }
+    sw.push_back(Ls);
+    for (int a = 1; a < dims; a++) {
+      if ((rc = plan_strided_sweep(p, a, 0, Ls)) != POISFFT_OK) { free_plan(p); return rc; }
+      sw.push_back(Ls);
+    }
+    memset(&Ls, 0, sizeof(Ls));
+    Ls.kind = 4;
+    PairDivideArgs& d = Ls.pda;
+    d.pitch = p->pitch;
+    d.ncols = p->ncols;
+    d.nx = p->nx;
+    d.ny = p->ny;
+    d.nz = p->nz;
+    d.per_y = dims >= 2 && bca[1] == POISFFT_P;
+    d.per_z = dims >= 3 && bca[2] == POISFFT_P;
+    double sc = 1.0;
+    for (int i = 0; i < 3; i++) sc *= p->axes[i].scale;
+    d.scale = sc;
+    d.singular = p->singular;
+    Ls.bytes = 2LL * p->ncols * (long long)p->ny * p->nz * (long long)(2 * p->esize);
+    sw.push_back(Ls);
+    for (int a = dims - 1; a >= 1; a--) {
+      if ((rc = plan_strided_sweep(p, a, 1, Ls)) != POISFFT_OK) { free_plan(p); return rc; }
+      sw.push_back(Ls);
+    }
+    if ((rc = plan_x_sweep(p, 1, Ls)) != POISFFT_OK) { free_plan(p); return rc; }
+    sw.push_back(Ls);
   } else {
   if ((rc = plan_x_sweep(p, 0, Ls)) != POISFFT_OK) { free_plan(p); return rc; }
   sw.push_back(Ls);
@@ -752,6 +784,11 @@ int poisfft_plan_create(poisfft_plan** out, int dims, const int64_t n[], const d
       L.xa.perm = p->perm[0];
       L.xa.ws = p->ws;
       L.xa.err = p->err;
+    } else if (L.kind == 4) {
+      L.pda.data = p->ws;
+      L.pda.lam_x = p->lam[0];
+      L.pda.lam_y = p->lam[1];
+      L.pda.lam_z = p->lam[2];
     } else if (L.kind == 1) {
       const int a = L.sa.axis_dim;
       L.sa.tables = p->tables[a];
@@ -846,8 +883,11 @@ int poisfft_launch_info(const poisfft_plan* p, int i, int64_t out[4]) {
   if (!p || !out || i < 0 || i >= (int)p->sweeps.size()) return POISFFT_ERR_INVALID_ARG;
   const SweepLaunch& L = p->sweeps[i];
   out[0] = L.bytes;
-  out[1] = (L.kind == 0 || L.kind == 2) ? 0 : 1;
-  if (L.kind >= 2) {
+  out[1] = (L.kind == 0 || L.kind == 2) ? 0 : (L.kind == 4 ? 2 : 1);
+  if (L.kind == 4) {
+    out[2] = 2;
+    out[3] = 0;
+  } else if (L.kind >= 2) {
     out[2] = L.fmode;
     out[3] = L.axis;
   } else {

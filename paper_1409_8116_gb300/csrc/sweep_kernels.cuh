@@ -231,6 +231,40 @@ __global__ void __launch_bounds__(kThreads) strided_sweep_kernel(const __grid_co
 }
 
 // ---------------------------------------------------------------------------
+// eigenvalue divide for packed real x columns with periodic y or z
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) pair_divide_kernel(const PairDivideArgs a) {
+  const long long total = (long long)a.ncols * a.ny * a.nz;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int c = (int)(e % a.ncols);
+  const long long r = e / a.ncols;
+  const int y = (int)(r % a.ny);
+  const int z = (int)(r / a.ny);
+  const int yn = a.per_y ? (a.ny - y) % a.ny : y;
+  const int zn = a.per_z ? (a.nz - z) % a.nz : z;
+  if (z > zn || (z == zn && y > yn)) return;  // the mirror element's thread does the pair
+  cx<T>* ws = reinterpret_cast<cx<T>*>(a.data);
+  const long long i1 = ((long long)z * a.ny + y) * a.pitch + c;
+  const long long i2 = ((long long)zn * a.ny + yn) * a.pitch + c;
+  const cx<T> z1 = ws[i1];
+  const cx<T> z2 = ws[i2];
+  // A(k) = (Z1 + conj Z2)/2, B(k) = (Z1 - conj Z2)/(2i)
+  const cx<T> A = mkc<T>(T(0.5) * (z1.x + z2.x), T(0.5) * (z1.y - z2.y));
+  const cx<T> B = mkc<T>(T(0.5) * (z1.y + z2.y), T(0.5) * (z2.x - z1.x));
+  const T* lx = reinterpret_cast<const T*>(a.lam_x);
+  const T lyz = reinterpret_cast<const T*>(a.lam_y)[y] + reinterpret_cast<const T*>(a.lam_z)[z];
+  const int kxa = 2 * c, kxb = 2 * c + 1;
+  T fa = T(0), fb = T(0);
+  if (kxa < a.nx && !(a.singular && kxa == 0 && y == 0 && z == 0)) fa = T(a.scale) / (lx[kxa] + lyz);
+  if (kxb < a.nx) fb = T(a.scale) / (lx[kxb] + lyz);
+  // Z'(k) = fa A + i fb B; at the mirror A and B are conjugated (Hermitian)
+  ws[i1] = mkc<T>(fa * A.x - fb * B.y, fa * A.y + fb * B.x);
+  if (i2 != i1) ws[i2] = mkc<T>(fa * A.x + fb * B.y, fb * B.x - fa * A.y);
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -249,6 +283,14 @@ cudaError_t launch_strided_sweep(const CUtensorMap& map, const StridedArgs& a, u
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<grid, kThreads, smem, s>>>(map, a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pair_divide(const PairDivideArgs& a, cudaStream_t s) {
+  const long long total = (long long)a.ncols * a.ny * a.nz;
+  const unsigned grid = (unsigned)((total + 255) / 256);
+  pair_divide_kernel<T><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

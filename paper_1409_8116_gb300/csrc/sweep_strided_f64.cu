@@ -4,4 +4,5 @@
 
 namespace pf {
 template cudaError_t launch_strided_sweep<double>(const CUtensorMap&, const StridedArgs&, unsigned, size_t, cudaStream_t);
+template cudaError_t launch_pair_divide<double>(const PairDivideArgs&, cudaStream_t);
 }  // namespace pf
