@@ -93,6 +93,18 @@ int poisfft_plan_create(poisfft_plan** out, int dims, const int64_t n[], const d
  * phi has zero mean (trapezoid-weighted along NR axes). */
 int poisfft_solve(poisfft_plan* plan, void* phi, const void* g, void* stream);
 
+/* The same solve on arrays that are part of larger arrays, e.g. fields with
+ * ghost cells (Sec. 3: the right-hand side and the solution can be a subset
+ * of a larger array).  phi and g point at element (0,0,0) of the grid;
+ * element (i,j,k) is at offset i + j*ld[0] + k*ld[1] (ld in elements).
+ *   ld[0] >= n[0] (y rows), ld[1] >= ld[0]*n[1] (z planes); entries for
+ *   axes the plan does not have are ignored.
+ * Elements outside the grid (ghost cells) are neither read nor written.
+ * phi == g with equal strides is allowed.  POISFFT_ERR_INVALID_ARG for
+ * strides that would overlap rows or planes. */
+int poisfft_solve_strided(poisfft_plan* plan, void* phi, const int64_t phi_ld[2], const void* g, const int64_t g_ld[2],
+                          void* stream);
+
 /* The same solve from and to HOST memory: copies g to the device, solves,
  * copies phi back, all on `stream`, then synchronises the stream.  Pinned
  * host buffers give full copy bandwidth; pageable ones work too.  Device

@@ -43,6 +43,7 @@ EXPORTED = [
     "poisfft_profile_read",
     "poisfft_launch_info",
     "poisfft_solve_noalloc",
+    "poisfft_solve_strided",
 ]
 
 
@@ -85,6 +86,9 @@ def _load():
                                           ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.poisfft_solve_noalloc.restype = ctypes.c_int
+    lib.poisfft_solve_strided.argtypes = [ctypes.c_void_p, ctypes.c_void_p, i64p, ctypes.c_void_p, i64p,
+                                          ctypes.c_void_p]
+    lib.poisfft_solve_strided.restype = ctypes.c_int
     return lib
 
 
@@ -184,6 +188,15 @@ class Plan:
         rc = solve(self._p, phi, g, stream)
         if rc != OK:
             raise PoisFFTError(rc, "poisfft_solve")
+
+    def solve_strided(self, phi, phi_ld, g, g_ld, stream=None):
+        """phi, g: addresses (or tensors) of element (0,0,0); *_ld = (row, plane)
+        strides in elements of the enclosing arrays."""
+        pl = (ctypes.c_int64 * 2)(*[int(v) for v in phi_ld])
+        gl = (ctypes.c_int64 * 2)(*[int(v) for v in g_ld])
+        rc = lib.poisfft_solve_strided(self._p, _ptr(phi), pl, _ptr(g), gl, _stream(stream))
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_solve_strided")
 
     def solve_host(self, phi, g, stream=None):
         rc = solve_host(self._p, phi, g, stream)

@@ -66,6 +66,8 @@ struct FastXArgs {
   const float* g;
   float* phi;
   float2* ws;
+  long long g_sy, g_sz;    // element strides of g between y rows and z planes
+  long long phi_sy, phi_sz;
 };
 
 // position of grid plane j in the even/odd reordering of an axis of length n
@@ -321,8 +323,8 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 2 : 3) fast_x_kernel(const Fa
     if (bi < R2) {
       const int j = bi;
       float2 u[R1];
-      const float* ga = a.g + ra * M;
-      const float* gb = a.g + rb * M;
+      const float* ga = a.g + (ra % a.ny) * a.g_sy + (ra / a.ny) * a.g_sz;
+      const float* gb = a.g + (rb % a.ny) * a.g_sy + (rb / a.ny) * a.g_sz;
 #pragma unroll
       for (int q = 0; q < R1; q++) u[q] = make_float2(va ? ga[j + R2 * q] : 0.f, vb ? gb[j + R2 * q] : 0.f);
       Dft<float, R1, false>::run(u);
@@ -403,8 +405,8 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 2 : 3) fast_x_kernel(const Fa
         for (int q = 1; q < R1; q++) u[q] = cmulc<float>(u[q], __ldg(&a.tw[q * R2 + j]));
       }
       Dft<float, R1, true>::run(u);
-      float* pa = a.phi + ra * M;
-      float* pb = a.phi + rb * M;
+      float* pa = a.phi + (ra % a.ny) * a.phi_sy + (ra / a.ny) * a.phi_sz;
+      float* pb = a.phi + (rb % a.ny) * a.phi_sy + (rb / a.ny) * a.phi_sz;
 #pragma unroll
       for (int s = 0; s < R1; s++) {
         if (va) pa[j + R2 * s] = u[s].x;

@@ -71,6 +71,9 @@ struct XArgs {
   void* phi;
   void* ws;
   int* err;
+  int ny;                 // rows per z plane (row r = y + ny*z)
+  long long g_sy, g_sz;   // element strides of g between y rows and z planes
+  long long phi_sy, phi_sz;
 };
 
 // Strided-axis (y or z) sweep on the complex workspace [nz][ny][pitch].

@@ -606,8 +606,13 @@ int record_event(poisfft_plan* p, cudaStream_t st) {
   return cudaEventRecord(ev, st) == cudaSuccess ? POISFFT_OK : POISFFT_ERR_CUDA;
 }
 
+// Element strides of g and phi between y rows and z planes (dense: nx, nx*ny).
+struct FieldStrides {
+  long long g_sy, g_sz, phi_sy, phi_sz;
+};
+
 template <typename T>
-int enqueue(poisfft_plan* p, void* phi, const void* g, cudaStream_t st) {
+int enqueue(poisfft_plan* p, void* phi, const void* g, cudaStream_t st, const FieldStrides& fs) {
   for (auto& L : p->sweeps) {
     if (p->profiling && record_event(p, st) != POISFFT_OK) return POISFFT_ERR_CUDA;
     cudaError_t e;
@@ -615,6 +620,11 @@ int enqueue(poisfft_plan* p, void* phi, const void* g, cudaStream_t st) {
       XArgs a = L.xa;
       a.g = g;
       a.phi = phi;
+      a.ny = p->ny;
+      a.g_sy = fs.g_sy;
+      a.g_sz = fs.g_sz;
+      a.phi_sy = fs.phi_sy;
+      a.phi_sz = fs.phi_sz;
       e = launch_x_sweep<T>(a, L.grid, L.smem, st);
     } else if (L.kind == 1) {
       e = launch_strided_sweep<T>(p->maps[L.map], L.sa, L.grid, L.smem, st);
@@ -624,6 +634,10 @@ int enqueue(poisfft_plan* p, void* phi, const void* g, cudaStream_t st) {
       fast::FastXArgs a = L.fxa;
       a.g = static_cast<const float*>(g);
       a.phi = static_cast<float*>(phi);
+      a.g_sy = fs.g_sy;
+      a.g_sz = fs.g_sz;
+      a.phi_sy = fs.phi_sy;
+      a.phi_sz = fs.phi_sz;
       e = launch_fast_x(L.M, L.fmode, a, L.grid, L.smem, st);
     } else {
       e = launch_fast_strided(L.M, L.w, L.fmode, L.fkind, p->maps[L.map], L.fsa, L.grid, L.smem, st);
@@ -632,6 +646,12 @@ int enqueue(poisfft_plan* p, void* phi, const void* g, cudaStream_t st) {
   }
   if (p->profiling && record_event(p, st) != POISFFT_OK) return POISFFT_ERR_CUDA;
   return POISFFT_OK;
+}
+
+template <typename T>
+int enqueue(poisfft_plan* p, void* phi, const void* g, cudaStream_t st) {
+  const long long nx = p->nx, nxy = (long long)p->nx * p->ny;
+  return enqueue<T>(p, phi, g, st, FieldStrides{nx, nxy, nx, nxy});
 }
 
 }  // namespace
@@ -810,6 +830,19 @@ int poisfft_solve(poisfft_plan* p, void* phi, const void* g, void* stream) {
   if (((uintptr_t)phi % p->esize) != 0 || ((uintptr_t)g % p->esize) != 0) return POISFFT_ERR_MISALIGNED;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   return p->esize == 4 ? enqueue<float>(p, phi, g, st) : enqueue<double>(p, phi, g, st);
+}
+
+int poisfft_solve_strided(poisfft_plan* p, void* phi, const int64_t phi_ld[2], const void* g, const int64_t g_ld[2],
+                          void* stream) {
+  if (!p || !phi || !g || !phi_ld || !g_ld) return POISFFT_ERR_INVALID_ARG;
+  if (((uintptr_t)phi % p->esize) != 0 || ((uintptr_t)g % p->esize) != 0) return POISFFT_ERR_MISALIGNED;
+  const long long nx = p->nx, ny = p->ny;
+  const long long gy = p->dims >= 2 ? g_ld[0] : nx, pyy = p->dims >= 2 ? phi_ld[0] : nx;
+  const long long gz = p->dims >= 3 ? g_ld[1] : gy * ny, pz = p->dims >= 3 ? phi_ld[1] : pyy * ny;
+  if (gy < nx || pyy < nx || gz < gy * ny || pz < pyy * ny) return POISFFT_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const FieldStrides fs{gy, gz, pyy, pz};
+  return p->esize == 4 ? enqueue<float>(p, phi, g, st, fs) : enqueue<double>(p, phi, g, st, fs);
 }
 
 int poisfft_solve_host(poisfft_plan* p, void* phi_host, const void* g_host, void* stream) {

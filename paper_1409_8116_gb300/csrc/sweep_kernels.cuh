@@ -48,14 +48,16 @@ __global__ void __launch_bounds__(kThreads, 2) x_sweep_kernel(const XArgs a) {
   if (a.mode == 0 || !a.r2c) {
     // complex line (row a, row b) in source order
     const T* src = reinterpret_cast<const T*>(a.mode == 0 ? a.g : a.ws);
-    const long long ld = a.mode == 0 ? (long long)nx : a.ws_ld;
     const int total = a.lines * nx;
     for (int e = threadIdx.x; e < total; e += kThreads) {
       const int l = e / nx;
       const int j = e - l * nx;
       const long long ra = row0 + 2 * l, rb = ra + 1;
-      const T va = ra < a.nrows ? src[ra * ld + j] : T(0);
-      const T vb = rb < a.nrows ? src[rb * ld + j] : T(0);
+      // g rows may sit inside a larger array (strides g_sy, g_sz)
+      const long long oa = a.mode == 0 ? (ra % a.ny) * a.g_sy + (ra / a.ny) * a.g_sz : ra * a.ws_ld;
+      const long long ob = a.mode == 0 ? (rb % a.ny) * a.g_sy + (rb / a.ny) * a.g_sz : rb * a.ws_ld;
+      const T va = ra < a.nrows ? src[oa + j] : T(0);
+      const T vb = rb < a.nrows ? src[ob + j] : T(0);
       buf[lay.idx(j, l)] = mkc<T>(va, vb);
     }
   } else {
@@ -102,15 +104,16 @@ __global__ void __launch_bounds__(kThreads, 2) x_sweep_kernel(const XArgs a) {
     }
   } else {
     T* dst = reinterpret_cast<T*>(a.mode == 0 ? a.ws : a.phi);
-    const long long ld = a.mode == 0 ? a.ws_ld : (long long)nx;
     const int total = a.lines * nx;
     for (int e = threadIdx.x; e < total; e += kThreads) {
       const int l = e / nx;
       const int k = e - l * nx;
       const long long ra = row0 + 2 * l, rb = ra + 1;
+      const long long oa = a.mode == 0 ? ra * a.ws_ld : (ra % a.ny) * a.phi_sy + (ra / a.ny) * a.phi_sz;
+      const long long ob = a.mode == 0 ? rb * a.ws_ld : (rb % a.ny) * a.phi_sy + (rb / a.ny) * a.phi_sz;
       const cx<T> v = post_value<T>(buf, lay, kind, nx, k, l, mk, perm);
-      if (ra < a.nrows) dst[ra * ld + k] = v.x;
-      if (rb < a.nrows) dst[rb * ld + k] = v.y;
+      if (ra < a.nrows) dst[oa + k] = v.x;
+      if (rb < a.nrows) dst[ob + k] = v.y;
     }
   }
 }
