@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(W.WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(W.WORKLOADS) + sorted(W.BATCHES))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 error check of the solution")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -379,10 +379,96 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """Batched workload: every step solves all problems once through the
+    batch's CUDA graph.  Also times the plain form (the same problems one
+    after another, no graph) for the speedup."""
+    import torch
+
+    from paper_1409_8116_gb300 import binding as pb
+
+    spec = W.BATCHES[args.workload]
+    probs = W.batch_problems(spec["count"], spec["seed"])
+    npts = sum(int(np.prod(p["n"])) for p in probs)
+    t0 = time.perf_counter()
+    batch = pb.Batch([(p["n"], p["Ls"], p["bcs"]) for p in probs], spec["approx"], pb.F32)
+    t_create = time.perf_counter() - t0
+    gs = [torch.from_numpy(W.normal(tuple(reversed(p["n"])), p["gseed"], dtype=np.float32)).cuda() for p in probs]
+    phis = [torch.empty_like(x) for x in gs]
+    stream = torch.cuda.Stream()
+    for _ in range(args.warmup):
+        batch.solve(phis, gs, stream)
+    stream.synchronize()
+    assert batch.check(stream) == pb.OK
+
+    def timed(fn, steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn(phis, gs, stream)
+        e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1)
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    ms_graph = timed(batch.solve, args.steps)
+    clocks = sampler.stop()
+    for _ in range(args.warmup):
+        batch.solve_sequential(phis, gs, stream)
+    ms_plain = timed(batch.solve_sequential, args.steps)
+    assert batch.check(stream) == pb.OK
+    value = throughput(npts, args.steps, 1, ms_graph / 1e3)
+    err = None
+    if not args.no_check:
+        from oracle import poisson as O
+
+        batch.solve(phis, gs, stream)
+        stream.synchronize()
+        worst = 0.0
+        for p, g, phi in list(zip(probs, gs, phis))[:64]:
+            ref = O.solve(g.cpu().numpy().astype(np.float64), p["bcs"], p["Ls"], spec["approx"], method="fft")
+            worst = max(worst, O.rel_max_error(phi.cpu().numpy(), ref))
+        err = worst
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import poisson as O
+
+        sample = sorted(probs, key=lambda p: int(np.prod(p["n"])))[:32]
+        t0 = time.perf_counter()
+        for p in sample:
+            O.solve(W.normal(tuple(reversed(p["n"])), p["gseed"], dtype=np.float64), p["bcs"], p["Ls"], spec["approx"])
+        dt = time.perf_counter() - t0
+        cpu = {"value": sum(int(np.prod(p["n"])) for p in sample) / dt, "unit": UNIT, "cores": os.cpu_count(),
+               "kind": "oracle", "sample": "FP64 oracle (dense Table-1 matrices) on the 32 smallest problems of the "
+                                           f"batch ({dt:.1f} s)"}
+    peak, peak_kind = load_peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_graph / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "problems": len(probs), "points": npts,
+                   "dims2": sum(p["dims"] == 2 for p in probs), "approx": "fd2",
+                   "l2": "inputs larger than L2 (2.7 GB over the batch)"},
+        "plain_ms_per_step": ms_plain / args.steps, "speedup_vs_plain": ms_plain / ms_graph,
+        "create_s": t_create, "max_rel_err_vs_fp64_first64": err,
+        "roofline": {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None,
+                     "kernel": "batch graph (per-launch timing not available inside a graph)",
+                     "peak_source": f"{peak_kind} hbm_gbs"},
+        "cpu_baseline": cpu, "e2e": None, "gpu_launches": None, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    batch.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in W.BATCHES:
+        return run_batch(args)
     return run_ours(args)
 
 

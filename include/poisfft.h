@@ -161,6 +161,37 @@ int poisfft_plan_info(const poisfft_plan* plan, int64_t info[4]);
 int poisfft_solve_noalloc(int dims, const int64_t n[], const double L[], const int bc[], int approx, int dtype,
                           void* phi, const void* g, void* stream);
 
+/* Tune the tile shapes of the plan's general-path launches on the device
+ * (strided sweeps: w, w/2, w/4 columns per tile; x sweeps: l, l/2, l/4 line
+ * pairs per CTA; three timed runs each, the fastest kept).  Allocates two
+ * temporary fields, synchronises `stream`, leaves the workspace zeroed.
+ * Plans on the specialised kernels keep their fixed shapes.  No paper
+ * counterpart.  Returns POISFFT_OK, ALLOC or CUDA. */
+int poisfft_plan_autotune(poisfft_plan* plan, void* stream);
+
+/* ---- Batched solves (many independent problems; no paper counterpart) ----
+ * poisfft_batch_create: one plan per problem i with dims[i], n[3i..3i+2],
+ *   L[3i..3i+2], bc[6i..6i+5] (entries beyond dims[i] ignored), a shared
+ *   approx and dtype; every plan is autotuned (poisfft_plan_autotune).
+ *   Fails with the first failing plan's status.
+ * poisfft_batch_solve: solves every problem (phi[i], g[i] as in
+ *   poisfft_solve) on `stream`.  The problems' launches run on forked
+ *   streams inside one CUDA graph, captured on the first call and replayed
+ *   while the pointers and the stream are unchanged (re-captured otherwise).
+ *   Capture happens on `stream`, so `stream` must not be the legacy default
+ *   stream (use a created stream).
+ * poisfft_batch_solve_sequential: the same problems one after another on
+ *   `stream` without a graph (the plain form, for comparison).
+ * poisfft_batch_check: poisfft_check over all plans (synchronises).
+ * poisfft_batch_destroy: frees the plans, streams and graph. */
+typedef struct poisfft_batch poisfft_batch;
+int poisfft_batch_create(poisfft_batch** out, int count, const int dims[], const int64_t n[], const double L[],
+                         const int bc[], int approx, int dtype);
+int poisfft_batch_solve(poisfft_batch* batch, void* const phi[], const void* const g[], void* stream);
+int poisfft_batch_solve_sequential(poisfft_batch* batch, void* const phi[], const void* const g[], void* stream);
+int poisfft_batch_check(poisfft_batch* batch, void* stream);
+int poisfft_batch_destroy(poisfft_batch* batch);
+
 /* Per-launch timing for benchmarks (no paper counterpart; measurement aid).
  * When enabled, every solve records a CUDA event on its stream before each
  * kernel launch and after the last one.  Host cost: one event record per

@@ -44,6 +44,12 @@ EXPORTED = [
     "poisfft_launch_info",
     "poisfft_solve_noalloc",
     "poisfft_solve_strided",
+    "poisfft_plan_autotune",
+    "poisfft_batch_create",
+    "poisfft_batch_solve",
+    "poisfft_batch_solve_sequential",
+    "poisfft_batch_check",
+    "poisfft_batch_destroy",
 ]
 
 
@@ -89,6 +95,20 @@ def _load():
     lib.poisfft_solve_strided.argtypes = [ctypes.c_void_p, ctypes.c_void_p, i64p, ctypes.c_void_p, i64p,
                                           ctypes.c_void_p]
     lib.poisfft_solve_strided.restype = ctypes.c_int
+    lib.poisfft_plan_autotune.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.poisfft_plan_autotune.restype = ctypes.c_int
+    vpp = ctypes.POINTER(ctypes.c_void_p)
+    lib.poisfft_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                         i64p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.c_int, ctypes.c_int]
+    lib.poisfft_batch_create.restype = ctypes.c_int
+    for nm in ("poisfft_batch_solve", "poisfft_batch_solve_sequential"):
+        getattr(lib, nm).argtypes = [ctypes.c_void_p, vpp, vpp, ctypes.c_void_p]
+        getattr(lib, nm).restype = ctypes.c_int
+    lib.poisfft_batch_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.poisfft_batch_check.restype = ctypes.c_int
+    lib.poisfft_batch_destroy.argtypes = [ctypes.c_void_p]
+    lib.poisfft_batch_destroy.restype = ctypes.c_int
     return lib
 
 
@@ -224,6 +244,11 @@ class Plan:
                             mode=("forward", "backward", "fused")[v[2]], axis="xyz"[v[3]]))
         return out
 
+    def autotune(self, stream=None):
+        rc = lib.poisfft_plan_autotune(self._p, _stream(stream))
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_plan_autotune")
+
     def profile(self, enable=True):
         rc = lib.poisfft_profile_enable(self._p, 1 if enable else 0)
         if rc != OK:
@@ -243,6 +268,66 @@ class Plan:
         if self._p:
             destroy(self._p)
             self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Many independent problems solved through one CUDA graph.
+
+    problems: sequence of (n, L, bc) with per-problem dims = len(n)."""
+
+    def __init__(self, problems, approx=FD2, dtype=F32):
+        cnt = len(problems)
+        dims = (ctypes.c_int * cnt)()
+        n = (ctypes.c_int64 * (3 * cnt))()
+        L = (ctypes.c_double * (3 * cnt))()
+        bc = (ctypes.c_int * (6 * cnt))()
+        for i, (nn, LL, bb) in enumerate(problems):
+            d = len(nn)
+            dims[i] = d
+            for a in range(3):
+                n[3 * i + a] = int(nn[a]) if a < d else 1
+                L[3 * i + a] = float(LL[a]) if a < d else 1.0
+                bc[6 * i + 2 * a] = bc[6 * i + 2 * a + 1] = int(bb[a]) if a < d else 0
+        h = ctypes.c_void_p()
+        rc = lib.poisfft_batch_create(ctypes.byref(h), cnt, dims, n, L, bc, int(approx), int(dtype))
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_batch_create")
+        self._b = h
+        self.count = cnt
+
+    def _ptrs(self, xs):
+        arr = (ctypes.c_void_p * self.count)(*[_ptr(x) for x in xs])
+        return arr
+
+    def solve(self, phis, gs, stream=None):
+        rc = lib.poisfft_batch_solve(self._b, self._ptrs(phis), self._ptrs(gs), _stream(stream))
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_batch_solve")
+
+    def solve_sequential(self, phis, gs, stream=None):
+        rc = lib.poisfft_batch_solve_sequential(self._b, self._ptrs(phis), self._ptrs(gs), _stream(stream))
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_batch_solve_sequential")
+
+    def check(self, stream=None):
+        return lib.poisfft_batch_check(self._b, _stream(stream))
+
+    def close(self):
+        if self._b:
+            lib.poisfft_batch_destroy(self._b)
+            self._b = None
 
     def __del__(self):
         try:

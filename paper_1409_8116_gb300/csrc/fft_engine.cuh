@@ -283,6 +283,59 @@ __device__ __noinline__ void dif_pass_generic(cx<T>* __restrict__ buf, cx<T>* __
   __syncthreads();
 }
 
+// Decimation-in-time pass (the transpose of dif_pass): butterfly (block, j)
+// multiplies input q by exp(-+2 pi i j q / L), takes the radix-R DFT and
+// writes output s back to block*L + j + s*(L/R).  Run in the reverse order
+// of the DIF passes, DIT takes the DIF output arrangement to natural order.
+template <typename T, int R, bool INV, class LAY>
+__device__ __noinline__ void dit_pass(cx<T>* __restrict__ buf, const LAY lay, int M, int ncol, int L,
+                                      const cx<T>* __restrict__ tw) {
+  const int Lr = L / R;
+  const int nbl = M / R;
+  const int nb = nbl * ncol;
+  for (int b = threadIdx.x; b < nb; b += kThreads) {
+    int t, c;
+    lay.split(b, nbl, t, c);
+    const int blk = t / Lr;
+    const int j = t - blk * Lr;
+    const int base = blk * L + j;
+    cx<T> u[R];
+#pragma unroll
+    for (int q = 0; q < R; q++) u[q] = buf[lay.idx(base + q * Lr, c)];
+    if (j != 0) {
+#pragma unroll
+      for (int q = 1; q < R; q++) {
+        const cx<T> w = tw[(q - 1) * Lr + j];
+        u[q] = INV ? cmulc<T>(u[q], w) : cmul<T>(u[q], w);
+      }
+    }
+    Dft<T, R, INV>::run(u);
+#pragma unroll
+    for (int s = 0; s < R; s++) buf[lay.idx(base + s * Lr, c)] = u[s];
+  }
+  __syncthreads();
+}
+
+// DIT passes of a power-of-two plan (used by the Bluestein convolution).
+template <typename T, bool INV, int EMAX, class LAY>
+__device__ __forceinline__ void run_passes_dit(cx<T>* buf, const LAY lay, const FftDesc& f, int ncol,
+                                               const cx<T>* __restrict__ tables) {
+  for (int ps = f.npass - 1; ps >= 0; ps--) {
+    const int R = f.radix[ps];
+    const int L = f.p[ps];
+    const cx<T>* tw = tables + f.tw_off[ps];
+    switch (R) {
+      case 2: dit_pass<T, 2, INV>(buf, lay, f.M, ncol, L, tw); break;
+      case 4: dit_pass<T, 4, INV>(buf, lay, f.M, ncol, L, tw); break;
+      case 8: dit_pass<T, 8, INV>(buf, lay, f.M, ncol, L, tw); break;
+      case 16: dit_pass<T, 16, INV>(buf, lay, f.M, ncol, L, tw); break;
+      default:
+        if constexpr (EMAX >= 32) dit_pass<T, 32, INV>(buf, lay, f.M, ncol, L, tw);
+        break;
+    }
+  }
+}
+
 template <typename T, bool INV, int EMAX, class LAY>
 __device__ __forceinline__ void run_passes_dir(cx<T>* buf, cx<T>* scratch, const LAY lay, const FftDesc& f, int ncol,
                                                const cx<T>* __restrict__ tables) {
@@ -421,6 +474,57 @@ __device__ __forceinline__ void pre_tile(cx<T>* buf, const LAY lay, int kind, in
       lay.split(e, M, m, c);
       buf[lay.idx(m, c)] = v[j];
     }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Bluestein (chirp-z) FFT of length M through a length-L convolution
+// ---------------------------------------------------------------------------
+// X_k = conj(c_k) sum_j (x_j conj(c_j)) c_{k-j},  c_m = exp(i pi m^2 / M)
+// (Bluestein 1970): the sum is a circular convolution of length L >= 2M-1,
+// done as DIF(L), a pointwise product with the precomputed kernel spectrum,
+// and an inverse DIT(L).  The FFT input x_j is the pre-processing value of
+// the transform `kind` gathered from the source lines in `src`; the result
+// X_k (natural order, k < M) is left in `dst` rows 0..M-1 for post_value
+// with an identity permutation.  The inverse direction conjugates input and
+// output.  No staging: src and dst are different smem regions.
+template <typename T, int EMAX, class LS, class LD>
+__device__ __forceinline__ void bluestein_fft(const cx<T>* src, const LS ls, cx<T>* dst, const LD ld,
+                                              const AxisDesc& ax, int kind, int n, int ncol,
+                                              const cx<T>* __restrict__ tables, const cx<T>* __restrict__ mk) {
+  const int M = ax.blu_M;
+  const int L = ax.fft.M;
+  const bool inv = kind_uses_inverse_fft(kind);
+  const cx<T>* chirp = tables + ax.chirp_off;
+  const cx<T>* bhat = tables + ax.bhat_off;
+  const int total = L * ncol;
+  for (int e = threadIdx.x; e < total; e += kThreads) {
+    int j, c;
+    ld.split(e, L, j, c);
+    cx<T> v = czero<T>();
+    if (j < M) {
+      v = pre_value<T>(src, ls, kind, n, M, j, c, mk);
+      if (inv) v = cconj<T>(v);
+      v = cmulc<T>(v, chirp[j]);
+    }
+    dst[ld.idx(j, c)] = v;
+  }
+  __syncthreads();
+  run_passes_dir<T, false, EMAX>(dst, dst, ld, ax.fft, ncol, tables);
+  for (int e = threadIdx.x; e < total; e += kThreads) {
+    int p, c;
+    ld.split(e, L, p, c);
+    dst[ld.idx(p, c)] = cmul<T>(dst[ld.idx(p, c)], bhat[p]);
+  }
+  __syncthreads();
+  run_passes_dit<T, true, EMAX>(dst, ld, ax.fft, ncol, tables);
+  const int tm = M * ncol;
+  for (int e = threadIdx.x; e < tm; e += kThreads) {
+    int k, c;
+    ld.split(e, M, k, c);
+    cx<T> x = cmulc<T>(dst[ld.idx(k, c)], chirp[k]);
+    dst[ld.idx(k, c)] = inv ? cconj<T>(x) : x;
   }
   __syncthreads();
 }

@@ -52,6 +52,12 @@ struct AxisDesc {
   int kfwd, kinv;         // TKind of the forward and backward transforms
   int mk_off;             // offset of the Makhoul twiddles exp(-i pi k/(2n)), k < n; -1 if unused
   FftDesc fft;
+  // Bluestein (chirp-z) form of the length-M FFT, used when M has a large
+  // prime factor: a circular convolution of power-of-two length L >= 2M-1.
+  int blu;                // 1: use it (fft describes the length-L passes then)
+  int blu_M;              // the DFT length M
+  int chirp_off;          // c_m = exp(+i pi m^2 / M), m < M
+  int bhat_off;           // DFT_L of the chirp kernel / L, in DIF output order
 };
 
 // Contiguous-axis (x) sweep.  Rows of the field are processed in pairs: row a

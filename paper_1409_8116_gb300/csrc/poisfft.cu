@@ -64,9 +64,43 @@ double sin_pi_frac(long long num, long long den) {  // sin(pi num/den)
 // ---------------------------------------------------------------------------
 // per-axis transform description
 // ---------------------------------------------------------------------------
+constexpr int kBluesteinMinPrime = 41;  // larger prime factors go through Bluestein
+
+// In-place forward DFT (exp(-2 pi i jk/N)) of a power-of-two length, FP64,
+// iterative radix 2 with exactly reduced twiddles (host tables only).
+void host_fft_pow2(std::vector<double>& re, std::vector<double>& im) {
+  const int N = (int)re.size();
+  for (int i = 1, j = 0; i < N; i++) {
+    int bit = N >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) {
+      std::swap(re[i], re[j]);
+      std::swap(im[i], im[j]);
+    }
+  }
+  for (int len = 2; len <= N; len <<= 1) {
+    for (int k = 0; k < len / 2; k++) {
+      double s, c;
+      sincos_2pi_frac(k, len, &s, &c);
+      const double wr = c, wi = -s;
+      for (int i = k; i < N; i += len) {
+        const int j = i + len / 2;
+        const double tr = re[j] * wr - im[j] * wi, ti = re[j] * wi + im[j] * wr;
+        re[j] = re[i] - tr;
+        im[j] = im[i] - ti;
+        re[i] += tr;
+        im[i] += ti;
+      }
+    }
+  }
+}
+
 bool is_unrolled_radix(int r, int emax) {
   return r == 2 || r == 3 || r == 4 || r == 5 || r == 7 || r == 8 || r == 16 || (r == 32 && emax >= 32);
 }
+// Staging capacity of the general kernels per thread (complex elements);
+// must match Emax<T> in sweep_kernels.cuh.
 
 // Factor M into DIF passes: powers of two grouped into balanced radices
 // up to 32 (16 for FP64), then 3, 5, 7, then any other prime (direct DFT).
@@ -124,9 +158,22 @@ int build_axis(AxisPlan& ax, int bc, int n, double L, int approx, int emax, bool
       default: return POISFFT_ERR_INVALID_ARG;
     }
   }
-  d.fft.M = M;
   std::vector<int> radices;
   factor_passes(M, emax, radices);
+  // Bluestein when a prime factor would need a slow direct-DFT pass
+  int maxp = 1;
+  for (int R : radices)
+    if (!is_unrolled_radix(R, emax)) maxp = std::max(maxp, R);
+  const bool blu = maxp >= kBluesteinMinPrime;
+  int Mfft = M;
+  if (blu) {
+    Mfft = 1;
+    while (Mfft < 2 * M - 1) Mfft *= 2;
+    factor_passes(Mfft, emax, radices);
+  }
+  d.blu = blu ? 1 : 0;
+  d.blu_M = M;
+  d.fft.M = Mfft;
   if ((int)radices.size() > kMaxPass) return POISFFT_ERR_UNSUPPORTED_SIZE;
   d.fft.npass = (int)radices.size();
   ax.tab_re.clear();
@@ -134,8 +181,9 @@ int build_axis(AxisPlan& ax, int bc, int n, double L, int approx, int emax, bool
   ax.generic = false;
   auto push = [&](double re, double im) { ax.tab_re.push_back(re); ax.tab_im.push_back(im); };
   // register budget: the pre/post gathers stage EMAX elements per thread
-  const long long cap = (long long)kThreads * emax / M;
-  int Lb = M;  // block length of the pass
+  // (the Bluestein path stages nothing)
+  const long long cap = blu ? (1LL << 20) : (long long)kThreads * emax / M;
+  int Lb = Mfft;  // block length of the pass
   for (int i = 0; i < d.fft.npass; i++) {
     const int R = radices[i];
     d.fft.radix[i] = R;
@@ -162,16 +210,51 @@ int build_axis(AxisPlan& ax, int bc, int n, double L, int approx, int emax, bool
     Lb = Lr;
   }
   // digit reversal: FFT output k = s_1 + R_1 (s_2 + R_2 (...)) sits at sum_i s_i L_i / R_i
-  ax.perm.assign(M, 0);
-  for (int k = 0; k < M; k++) {
-    int rem = k, pos = 0, Li = M;
+  std::vector<int> perm(Mfft, 0);
+  for (int k = 0; k < Mfft; k++) {
+    int rem = k, pos = 0, Li = Mfft;
     for (int i = 0; i < d.fft.npass; i++) {
       const int R = d.fft.radix[i];
       pos += (rem % R) * (Li / R);
       rem /= R;
       Li /= R;
     }
-    ax.perm[k] = pos;
+    perm[k] = pos;
+  }
+  if (blu) {
+    // chirp c_m = exp(i pi m^2 / M) and the spectrum of the circulant kernel
+    // b_m = c_m (|m| < M, indices mod L), divided by L, in DIF output order
+    d.chirp_off = (int)ax.tab_re.size();
+    std::vector<double> cr(M), ci(M);
+    for (int m = 0; m < M; m++) {
+      double sn, c;
+      sincos_2pi_frac(((long long)m * m) % (2LL * M), 2LL * M, &sn, &c);
+      cr[m] = c;
+      ci[m] = sn;
+      push(c, sn);
+    }
+    std::vector<double> br(Mfft, 0.0), bi(Mfft, 0.0);
+    for (int m = 0; m < M; m++) {
+      br[m] = cr[m];
+      bi[m] = ci[m];
+      if (m > 0) {
+        br[Mfft - m] = cr[m];
+        bi[Mfft - m] = ci[m];
+      }
+    }
+    host_fft_pow2(br, bi);
+    d.bhat_off = (int)ax.tab_re.size();
+    std::vector<double> hr(Mfft), hi(Mfft);
+    for (int k = 0; k < Mfft; k++) {
+      hr[perm[k]] = br[k] / Mfft;
+      hi[perm[k]] = bi[k] / Mfft;
+    }
+    for (int k = 0; k < Mfft; k++) push(hr[k], hi[k]);
+    ax.perm.resize(M);
+    for (int k = 0; k < M; k++) ax.perm[k] = k;  // the Bluestein result is in natural order
+  } else {
+    d.chirp_off = d.bhat_off = -1;
+    ax.perm = perm;
   }
   if (d.kfwd == TK_DCT2 || d.kfwd == TK_DST2) {
     d.mk_off = (int)ax.tab_re.size();
@@ -278,7 +361,7 @@ struct poisfft_plan {
   void* lam[3] = {nullptr, nullptr, nullptr};
   int* perm[3] = {nullptr, nullptr, nullptr};
   int* err = nullptr;
-  CUtensorMap maps[2];
+  std::vector<CUtensorMap> maps;      // one per launch (strided launches use theirs)
   std::vector<SweepLaunch> sweeps;
   void* stage_g = nullptr;
   void* stage_phi = nullptr;
@@ -337,6 +420,23 @@ int upload_tables(poisfft_plan* p) {
   return POISFFT_OK;
 }
 
+// smem rows of one x line: the in-place line (plus a direct-DFT scratch
+// line), or the source line plus the Bluestein convolution buffer
+int x_line_ld(const poisfft_plan* p) { return p->axes[0].d.blu ? p->nx : p->axes[0].d.fft.M; }
+size_t x_per_line(const poisfft_plan* p) {
+  const AxisPlan& ax = p->axes[0];
+  const size_t cx = 2 * p->esize;
+  if (ax.d.blu) return (size_t)(p->nx + ax.d.fft.M) * cx;
+  return (size_t)ax.d.fft.M * cx * (ax.generic ? 2 : 1);
+}
+// smem bytes per tile column of a strided sweep with `rows_alloc` tile rows
+size_t strided_per_col(const poisfft_plan* p, int axis, int rows_alloc) {
+  const AxisPlan& ax = p->axes[axis];
+  const size_t cx = 2 * p->esize;
+  if (ax.d.blu) return (size_t)(rows_alloc + ax.d.fft.M) * cx;
+  return (size_t)rows_alloc * cx * (ax.generic ? 2 : 1);
+}
+
 // x sweep configuration
 int plan_x_sweep(poisfft_plan* p, int mode, SweepLaunch& L) {
   AxisPlan& ax = p->axes[0];
@@ -345,7 +445,7 @@ int plan_x_sweep(poisfft_plan* p, int mode, SweepLaunch& L) {
   const long long nrows = (long long)p->ny * p->nz;
   const long long pairs = (nrows + 1) / 2;
   long long lines = ax.max_ncol;
-  const size_t per_line = (size_t)M * cx * (ax.generic ? 2 : 1);
+  const size_t per_line = x_per_line(p);
   lines = std::min<long long>(lines, (long long)(kSmemTarget / per_line));
   lines = std::min<long long>(lines, pairs);
   if (lines < 1) {
@@ -361,7 +461,7 @@ int plan_x_sweep(poisfft_plan* p, int mode, SweepLaunch& L) {
   a.r2c = p->r2c;
   a.nx = p->nx;
   a.lines = (int)lines;
-  a.ld = M;
+  a.ld = x_line_ld(p);
   a.nrows = nrows;
   a.ws_ld = p->r2c ? p->pitch : 2LL * p->pitch;
   a.ws = p->ws;
@@ -388,8 +488,8 @@ int plan_strided_sweep(poisfft_plan* p, int axis, int mode, SweepLaunch& L) {
     box_h = (n + nbox - 1) / nbox;
     box_h = (box_h + 15) / 16 * 16;
   }
-  const int rows_alloc = std::max(M, nbox * box_h);
-  const size_t per_col = (size_t)rows_alloc * cx * (ax.generic ? 2 : 1);
+  const int rows_alloc = ax.d.blu ? nbox * box_h : std::max(M, nbox * box_h);
+  const size_t per_col = strided_per_col(p, axis, rows_alloc);
   long long w = std::min<long long>(ax.max_ncol, 128);
   w = std::min<long long>(w, pow2_ceil(p->ncols));
   w = std::min<long long>(w, (long long)(kSmemTarget / per_col));
@@ -583,7 +683,10 @@ int encode_maps(poisfft_plan* p) {
   const cuuint64_t row = (cuuint64_t)p->pitch * 2 * p->esize;
   const cuuint64_t gstride[2] = {row, row * (cuuint64_t)p->ny};
   const cuuint32_t estr[3] = {1, 1, 1};
-  for (auto& L : p->sweeps) {
+  p->maps.resize(p->sweeps.size());
+  for (size_t li = 0; li < p->sweeps.size(); li++) {
+    SweepLaunch& L = p->sweeps[li];
+    L.map = (int)li;
     if (L.kind != 1 && L.kind != 3) continue;
     const int w = L.kind == 1 ? L.sa.w : L.w;
     const int axis_dim = L.kind == 1 ? L.sa.axis_dim : L.axis;
@@ -712,7 +815,7 @@ int poisfft_plan_create(poisfft_plan** out, int dims, const int64_t n[], const d
   p->nz = (int)nn[2];
   p->esize = dtype == POISFFT_F32 ? 4 : 8;
   p->r2c = xper ? 1 : 0;
-  const int emax = dtype == POISFFT_F32 ? 32 : 16;
+  const int emax = dtype == POISFFT_F32 ? 40 : 16;
   bool sing = true;
   for (int a = 0; a < 3; a++) {
     const bool null_axis = a >= dims;
@@ -1064,7 +1167,7 @@ extern "C" int poisfft_solve_noalloc(int dims, const int64_t n[], const double L
   p->nz = (int)nn[2];
   p->esize = esize;
   p->r2c = xper ? 1 : 0;
-  const int emax = dtype == POISFFT_F32 ? 32 : 16;
+  const int emax = dtype == POISFFT_F32 ? 40 : 16;
   bool sing = true;
   int rc = POISFFT_OK;
   for (int a = 0; a < 3 && rc == POISFFT_OK; a++) {
@@ -1129,3 +1232,282 @@ extern "C" int poisfft_solve_noalloc(int dims, const int64_t n[], const double L
   release_noalloc_plan(p);
   return rc;
 }
+
+// ---------------------------------------------------------------------------
+// Autotuner of the general-path tile shapes
+// ---------------------------------------------------------------------------
+// For every launch of the general kernels the tuner times the planned tile
+// shape and up to two smaller ones (strided sweeps: w, w/2, w/4 columns;
+// x sweeps: l, l/2, l/4 line pairs per CTA) on the device, three runs each,
+// and keeps the fastest.  The specialised kernels have fixed, measured shapes.
+namespace {
+
+void set_strided_width(poisfft_plan* p, SweepLaunch& L, int w) {
+  StridedArgs& s = L.sa;
+  const size_t per_col = strided_per_col(p, s.axis_dim, s.rows_alloc);
+  s.w = w;
+  s.lw = ilog2(w);
+  s.ntile_c = (p->ncols + w - 1) / w;
+  s.bar_off = (int)(((size_t)w * per_col + 15) / 16 * 16);
+  L.grid = (unsigned)((long long)s.ntile_c * s.nouter);
+  L.smem = (size_t)s.bar_off + 16;
+}
+
+void set_x_lines(poisfft_plan* p, SweepLaunch& L, int lines) {
+  const size_t per_line = x_per_line(p);
+  const long long pairs = ((long long)p->ny * p->nz + 1) / 2;
+  L.xa.lines = lines;
+  L.grid = (unsigned)((pairs + lines - 1) / lines);
+  L.smem = (size_t)lines * per_line;
+}
+
+template <typename T>
+float time_launch(poisfft_plan* p, SweepLaunch& L, void* phi, const void* g, cudaStream_t st, cudaEvent_t e0,
+                  cudaEvent_t e1) {
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; rep++) {
+    cudaEventRecord(e0, st);
+    cudaError_t e;
+    if (L.kind == 0) {
+      XArgs a = L.xa;
+      a.g = g;
+      a.phi = phi;
+      a.ny = p->ny;
+      a.g_sy = a.phi_sy = p->nx;
+      a.g_sz = a.phi_sz = (long long)p->nx * p->ny;
+      e = launch_x_sweep<T>(a, L.grid, L.smem, st);
+    } else {
+      e = launch_strided_sweep<T>(p->maps[L.map], L.sa, L.grid, L.smem, st);
+    }
+    cudaEventRecord(e1, st);
+    if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = std::min(best, ms);
+  }
+  return best;
+}
+
+template <typename T>
+int autotune_plan(poisfft_plan* p, cudaStream_t st) {
+  void* g = nullptr;
+  void* phi = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = POISFFT_OK;
+  if (cudaMalloc(&g, p->field_bytes) != cudaSuccess || cudaMalloc(&phi, p->field_bytes) != cudaSuccess ||
+      cudaMemsetAsync(g, 0, p->field_bytes, st) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess)
+    rc = POISFFT_ERR_ALLOC;
+  const int wmin = p->esize == 4 ? 2 : 1;
+  for (size_t li = 0; rc == POISFFT_OK && li < p->sweeps.size(); li++) {
+    SweepLaunch& L = p->sweeps[li];
+    if (L.kind != 0 && L.kind != 1) continue;
+    const int base = L.kind == 0 ? L.xa.lines : L.sa.w;
+    int best = base;
+    float best_ms = 1e30f;
+    for (int div = 1; div <= 4; div *= 2) {
+      const int cand = base / div;
+      if (L.kind == 1 && cand < wmin) break;
+      if (L.kind == 0 && cand < 1) break;
+      if (L.kind == 1) {
+        set_strided_width(p, L, cand);
+        if ((rc = encode_maps(p)) != POISFFT_OK) break;
+      } else {
+        set_x_lines(p, L, cand);
+      }
+      const float ms = time_launch<T>(p, L, phi, g, st, e0, e1);
+      if (ms < 0.f) {
+        rc = POISFFT_ERR_CUDA;
+        break;
+      }
+      if (ms < best_ms * 0.97f) {  // smaller tiles must win clearly
+        best_ms = ms;
+        best = cand;
+      }
+    }
+    if (L.kind == 1) set_strided_width(p, L, best);
+    else set_x_lines(p, L, best);
+  }
+  if (rc == POISFFT_OK) rc = encode_maps(p);
+  if (rc == POISFFT_OK && cudaMemsetAsync(p->ws, 0, p->ws_bytes, st) != cudaSuccess) rc = POISFFT_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess && rc == POISFFT_OK) rc = POISFFT_ERR_CUDA;
+  if (g) cudaFree(g);
+  if (phi) cudaFree(phi);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaGetLastError();
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int poisfft_plan_autotune(poisfft_plan* p, void* stream) {
+  if (!p) return POISFFT_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  return p->esize == 4 ? autotune_plan<float>(p, st) : autotune_plan<double>(p, st);
+}
+
+// ---------------------------------------------------------------------------
+// Batched solves: many independent problems, one CUDA graph
+// ---------------------------------------------------------------------------
+// Each problem has its own plan (workspace, tables, tiles).  A solve records
+// every problem's launches on one of kBatchStreams forked streams (problems
+// assigned greedily by size so the streams carry similar work), joins them,
+// and replays that graph while the caller's pointers and stream stay the same.
+struct poisfft_batch {
+  std::vector<poisfft_plan*> plans;
+  std::vector<int> stream_of;          // problem -> forked stream
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const void*> g_cached;
+  std::vector<void*> phi_cached;
+  cudaStream_t stream_cached = nullptr;
+};
+
+namespace {
+
+constexpr int kBatchStreams = 8;
+
+void free_batch(poisfft_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+  for (poisfft_plan* p : b->plans) free_plan(p);
+  delete b;
+}
+
+int batch_record(poisfft_batch* b, void* const phi[], const void* const g[], cudaStream_t st) {
+  if (cudaEventRecord(b->fork, st) != cudaSuccess) return POISFFT_ERR_CUDA;
+  for (cudaStream_t s : b->streams)
+    if (cudaStreamWaitEvent(s, b->fork, 0) != cudaSuccess) return POISFFT_ERR_CUDA;
+  for (size_t i = 0; i < b->plans.size(); i++) {
+    const int rc = poisfft_solve(b->plans[i], phi[i], g[i], b->streams[b->stream_of[i]]);
+    if (rc != POISFFT_OK) return rc;
+  }
+  for (size_t s = 0; s < b->streams.size(); s++) {
+    if (cudaEventRecord(b->joins[s], b->streams[s]) != cudaSuccess) return POISFFT_ERR_CUDA;
+    if (cudaStreamWaitEvent(st, b->joins[s], 0) != cudaSuccess) return POISFFT_ERR_CUDA;
+  }
+  return POISFFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int poisfft_batch_create(poisfft_batch** out, int count, const int dims[], const int64_t n[], const double L[],
+                         const int bc[], int approx, int dtype) {
+  if (!out) return POISFFT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (count < 1 || !dims || !n || !L || !bc) return POISFFT_ERR_INVALID_ARG;
+  poisfft_batch* b = new (std::nothrow) poisfft_batch();
+  if (!b) return POISFFT_ERR_ALLOC;
+  std::vector<double> load;
+  for (int i = 0; i < count; i++) {
+    poisfft_plan* p = nullptr;
+    const int rc = poisfft_plan_create(&p, dims[i], n + 3 * (size_t)i, L + 3 * (size_t)i, bc + 6 * (size_t)i, approx,
+                                       dtype);
+    if (rc != POISFFT_OK) {
+      free_batch(b);
+      return rc;
+    }
+    b->plans.push_back(p);
+    const int rt = poisfft_plan_autotune(p, nullptr);
+    if (rt != POISFFT_OK) {
+      free_batch(b);
+      return rt;
+    }
+  }
+  const int ns = std::min(kBatchStreams, count);
+  load.assign(ns, 0.0);
+  // greedy assignment, largest problems first
+  std::vector<int> order(count);
+  for (int i = 0; i < count; i++) order[i] = i;
+  auto pts = [&](int i) { return (double)b->plans[i]->nx * b->plans[i]->ny * b->plans[i]->nz; };
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return pts(x) > pts(y); });
+  b->stream_of.assign(count, 0);
+  for (int i : order) {
+    const int s = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    b->stream_of[i] = s;
+    load[s] += pts(i);
+  }
+  for (int s = 0; s < ns; s++) {
+    cudaStream_t st;
+    cudaEvent_t ev;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { free_batch(b); return POISFFT_ERR_CUDA; }
+    b->streams.push_back(st);
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) { free_batch(b); return POISFFT_ERR_CUDA; }
+    b->joins.push_back(ev);
+  }
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) { free_batch(b); return POISFFT_ERR_CUDA; }
+  *out = b;
+  return POISFFT_OK;
+}
+
+int poisfft_batch_solve(poisfft_batch* b, void* const phi[], const void* const g[], void* stream) {
+  if (!b || !phi || !g) return POISFFT_ERR_INVALID_ARG;
+  const size_t cnt = b->plans.size();
+  for (size_t i = 0; i < cnt; i++) {
+    if (!phi[i] || !g[i]) return POISFFT_ERR_INVALID_ARG;
+    const size_t es = b->plans[i]->esize;
+    if (((uintptr_t)phi[i] % es) != 0 || ((uintptr_t)g[i] % es) != 0) return POISFFT_ERR_MISALIGNED;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  bool same = b->exec && st == b->stream_cached && b->g_cached.size() == cnt;
+  for (size_t i = 0; same && i < cnt; i++) same = b->g_cached[i] == g[i] && b->phi_cached[i] == phi[i];
+  if (!same) {
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) return POISFFT_ERR_CUDA;
+    const int rc = batch_record(b, phi, g, st);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+    if (rc != POISFFT_OK || ec != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return rc != POISFFT_OK ? rc : POISFFT_ERR_CUDA;
+    }
+    b->graph = graph;
+    if (cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) {
+      cudaGetLastError();
+      b->exec = nullptr;
+      return POISFFT_ERR_CUDA;
+    }
+    b->g_cached.assign(g, g + cnt);
+    b->phi_cached.assign(phi, phi + cnt);
+    b->stream_cached = st;
+  }
+  return cudaGraphLaunch(b->exec, st) == cudaSuccess ? POISFFT_OK : POISFFT_ERR_CUDA;
+}
+
+int poisfft_batch_solve_sequential(poisfft_batch* b, void* const phi[], const void* const g[], void* stream) {
+  if (!b || !phi || !g) return POISFFT_ERR_INVALID_ARG;
+  for (size_t i = 0; i < b->plans.size(); i++) {
+    const int rc = poisfft_solve(b->plans[i], phi[i], g[i], stream);
+    if (rc != POISFFT_OK) return rc;
+  }
+  return POISFFT_OK;
+}
+
+int poisfft_batch_check(poisfft_batch* b, void* stream) {
+  if (!b) return POISFFT_ERR_INVALID_ARG;
+  int worst = POISFFT_OK;
+  for (poisfft_plan* p : b->plans) {
+    const int rc = poisfft_check(p, stream);
+    if (rc != POISFFT_OK) worst = rc;
+  }
+  return worst;
+}
+
+int poisfft_batch_destroy(poisfft_batch* b) {
+  free_batch(b);
+  return POISFFT_OK;
+}
+
+}  // extern "C"

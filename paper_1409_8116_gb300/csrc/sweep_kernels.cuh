@@ -23,7 +23,7 @@
 namespace pf {
 
 template <typename T> struct Emax;
-template <> struct Emax<float> { static constexpr int value = 32; };
+template <> struct Emax<float> { static constexpr int value = 40; };
 template <> struct Emax<double> { static constexpr int value = 16; };
 
 // ---------------------------------------------------------------------------
@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(kThreads, 2) x_sweep_kernel(const XArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   const RowTile lay{a.ld};
-  cx<T>* scratch = buf + (size_t)a.lines * a.ld;  // used only by direct-DFT passes
+  cx<T>* scratch = buf + (size_t)a.lines * a.ld;  // direct-DFT scratch or the Bluestein buffer
   const cx<T>* tables = reinterpret_cast<const cx<T>*>(a.tables);
   const cx<T>* mk = a.ax.mk_off >= 0 ? tables + a.ax.mk_off : nullptr;
   const int* perm = a.perm;
@@ -81,9 +81,18 @@ __global__ void __launch_bounds__(kThreads, 2) x_sweep_kernel(const XArgs a) {
   }
   __syncthreads();
 
-  // ---- stage B/C: pre-processing gather and the FFT passes
-  pre_tile<T, EMAX>(buf, lay, kind, nx, M, a.lines, mk);
-  run_passes<T, EMAX>(buf, scratch, lay, a.ax.fft, a.lines, tables, kind_uses_inverse_fft(kind));
+  // ---- stage B/C: pre-processing gather and the FFT (in place, or Bluestein
+  // from the source lines into the convolution buffer)
+  cx<T>* res = buf;
+  RowTile lres = lay;
+  if (a.ax.blu) {
+    lres = RowTile{M};
+    bluestein_fft<T, EMAX>(buf, lay, scratch, lres, a.ax, kind, nx, a.lines, tables, mk);
+    res = scratch;
+  } else {
+    pre_tile<T, EMAX>(buf, lay, kind, nx, M, a.lines, mk);
+    run_passes<T, EMAX>(buf, scratch, lay, a.ax.fft, a.lines, tables, kind_uses_inverse_fft(kind));
+  }
 
   // ---- stage D: post-processing and store
   if (a.mode == 0 && a.r2c) {
@@ -94,8 +103,8 @@ __global__ void __launch_bounds__(kThreads, 2) x_sweep_kernel(const XArgs a) {
       const int l = e / nh;
       const int k = e - l * nh;
       const long long ra = row0 + 2 * l, rb = ra + 1;
-      const cx<T> z1 = buf[lay.idx(perm[k], l)];
-      const cx<T> z2 = buf[lay.idx(perm[k == 0 ? 0 : nx - k], l)];
+      const cx<T> z1 = res[lres.idx(perm[k], l)];
+      const cx<T> z2 = res[lres.idx(perm[k == 0 ? 0 : nx - k], l)];
       // A = (z1 + conj z2)/2,  B = (z1 - conj z2)/(2i)
       const cx<T> A = mkc<T>(T(0.5) * (z1.x + z2.x), T(0.5) * (z1.y - z2.y));
       const cx<T> B = mkc<T>(T(0.5) * (z1.y + z2.y), T(0.5) * (z2.x - z1.x));
@@ -111,9 +120,15 @@ __global__ void __launch_bounds__(kThreads, 2) x_sweep_kernel(const XArgs a) {
       const long long ra = row0 + 2 * l, rb = ra + 1;
       const long long oa = a.mode == 0 ? ra * a.ws_ld : (ra % a.ny) * a.phi_sy + (ra / a.ny) * a.phi_sz;
       const long long ob = a.mode == 0 ? rb * a.ws_ld : (rb % a.ny) * a.phi_sy + (rb / a.ny) * a.phi_sz;
-      const cx<T> v = post_value<T>(buf, lay, kind, nx, k, l, mk, perm);
+      const cx<T> v = post_value<T>(res, lres, kind, nx, k, l, mk, perm);
       if (ra < a.nrows) dst[oa + k] = v.x;
       if (rb < a.nrows) dst[ob + k] = v.y;
+      // odd nx: the padding half of the last packed column starts every solve
+      // at zero (a periodic y/z DFT would otherwise leave rounding noise there)
+      if (a.mode == 0 && k == nx - 1 && (nx & 1)) {
+        if (ra < a.nrows) dst[oa + nx] = T(0);
+        if (rb < a.nrows) dst[ob + nx] = T(0);
+      }
     }
   }
 }
@@ -138,7 +153,7 @@ __global__ void __launch_bounds__(kThreads) strided_sweep_kernel(const __grid_co
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + a.bar_off);
   const ColTile lay{a.w, a.lw};
-  cx<T>* scratch = buf + (size_t)a.rows_alloc * a.w;  // used only by direct-DFT passes
+  cx<T>* scratch = buf + (size_t)a.rows_alloc * a.w;  // direct-DFT scratch or the Bluestein buffer
   const cx<T>* tables = reinterpret_cast<const cx<T>*>(a.tables);
   const cx<T>* mk = a.ax.mk_off >= 0 ? tables + a.ax.mk_off : nullptr;
   const int* perm = a.perm;
@@ -176,13 +191,52 @@ __global__ void __launch_bounds__(kThreads) strided_sweep_kernel(const __grid_co
 
   if (a.mode != 2) {
     const int kind = a.mode == 0 ? a.ax.kfwd : a.ax.kinv;
-    pre_tile<T, EMAX>(buf, lay, kind, n, M, a.w, mk);
-    run_passes<T, EMAX>(buf, scratch, lay, a.ax.fft, a.w, tables, kind_uses_inverse_fft(kind));
+    cx<T>* res = buf;
+    if (a.ax.blu) {
+      bluestein_fft<T, EMAX>(buf, lay, scratch, lay, a.ax, kind, n, a.w, tables, mk);
+      res = scratch;
+    } else {
+      pre_tile<T, EMAX>(buf, lay, kind, n, M, a.w, mk);
+      run_passes<T, EMAX>(buf, scratch, lay, a.ax.fft, a.w, tables, kind_uses_inverse_fft(kind));
+    }
     const int total = n * a.w;
     for (int e = threadIdx.x; e < total; e += kThreads) {
       const int c = e & (a.w - 1);
       const int k = e >> a.lw;
-      if (c < ncol_valid) out[(size_t)k * a.s_axis + c] = post_value<T>(buf, lay, kind, n, k, c, mk, perm);
+      if (c < ncol_valid) out[(size_t)k * a.s_axis + c] = post_value<T>(res, lay, kind, n, k, c, mk, perm);
+    }
+    return;
+  }
+
+  if (a.ax.blu) {
+    // fused, Bluestein: forward into the buffer, divided spectrum back into
+    // the source rows, backward from there
+    const T* lin = reinterpret_cast<const T*>(a.lam_in);
+    const T* lax = reinterpret_cast<const T*>(a.lam_ax);
+    const T* lout = reinterpret_cast<const T*>(a.lam_out);
+    bluestein_fft<T, EMAX>(buf, lay, scratch, lay, a.ax, a.ax.kfwd, n, a.w, tables, mk);
+    const int total = n * a.w;
+    for (int e = threadIdx.x; e < total; e += kThreads) {
+      const int c = e & (a.w - 1);
+      const int k = e >> a.lw;
+      cx<T> x = post_value<T>(scratch, lay, a.ax.kfwd, n, k, c, mk, perm);
+      const int col = c0 + c;
+      if (a.packed) {
+        x.x *= eigen_factor<T>(a, lin, lax, lout, 2 * col, k, outer);
+        x.y *= eigen_factor<T>(a, lin, lax, lout, 2 * col + 1, k, outer);
+      } else {
+        const T f = eigen_factor<T>(a, lin, lax, lout, col, k, outer);
+        x.x *= f;
+        x.y *= f;
+      }
+      buf[lay.idx(k, c)] = x;
+    }
+    __syncthreads();
+    bluestein_fft<T, EMAX>(buf, lay, scratch, lay, a.ax, a.ax.kinv, n, a.w, tables, mk);
+    for (int e = threadIdx.x; e < total; e += kThreads) {
+      const int c = e & (a.w - 1);
+      const int k = e >> a.lw;
+      if (c < ncol_valid) out[(size_t)k * a.s_axis + c] = post_value<T>(scratch, lay, a.ax.kinv, n, k, c, mk, perm);
     }
     return;
   }

@@ -268,3 +268,25 @@ def test_pair_divide_tiling(pb, bcs):
             continue
         check(pb, shape, bcs, W.FD2, "f32", seed=15)
         check(pb, shape, bcs, W.SPECTRAL, "f64", seed=16)
+
+
+# ---------------------------------------------------------------------------
+# Bluestein: FFT lengths with a prime factor >= 41 (prime n, or 2(n+1), 2(n-1)
+# of the DST-I / DCT-I extensions) on every axis
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,bcs", [
+    ((101,), (W.P,)), ((88,), (W.DR,)), ((84,), (W.NR,)), ((97,), (W.DS,)), ((113,), (W.NS,)),
+    ((88, 101, 84), (W.DR, W.P, W.NR)),       # x extension 2*89, y prime, z extension 2*83
+    ((101, 60, 113), (W.P, W.DS, W.NS)),       # x prime (R2C), z prime
+    ((40, 88, 43), (W.NS, W.DR, W.P)),         # pair divide with Bluestein y and z
+], ids=lambda v: str(v))
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_bluestein_lengths(pb, n, bcs, dtype):
+    check(pb, tuple(reversed(n)), bcs, W.FD2, dtype, seed=17)
+
+
+def test_bluestein_large_2d_batch_case(pb):
+    """A batch problem that dominated the direct-DFT timings: y = DST-I with
+    n = 1800 (extension 2 * 1801)."""
+    check(pb, (1800, 1792), (W.DS, W.DR), W.FD2, "f32", seed=18, method="fft")

@@ -120,6 +120,45 @@ WORKLOADS = {
         dtype="f32", gen=("smooth_random_field", 3)),
 }
 
+# Batched workload: 512 independent problems (see batch_problems), FP32, FD2.
+BATCHES = {
+    "batched_512_f32": dict(count=512, seed=4, dtype="f32", approx=FD2),
+}
+
+
+def smooth_numbers(lo, hi, primes=(2, 3, 5, 7)):
+    """Integers in [lo, hi] whose prime factors all lie in `primes`."""
+    out = []
+    for n in range(lo, hi + 1):
+        m = n
+        for p in primes:
+            while m % p == 0:
+                m //= p
+        if m == 1:
+            out.append(n)
+    return out
+
+
+def batch_problems(count=512, seed=4, n2d=(64, 2048), n3d=(32, 256), max_points=None):
+    """Independent problems of the batched workload: half 2D with n in
+    [64, 2048] per axis, half 3D with n in [32, 256] per axis, every n
+    {2,3,5,7}-smooth; each axis draws its BC from all five kinds (P, DST-I,
+    DST-II, DCT-I, DCT-II); FD2 eigenvalues; L = 1 per axis.  Returns a list
+    of dicts (dims, n (x first), bcs, Ls, seed of g)."""
+    r = rng(seed)
+    s2 = smooth_numbers(*n2d)
+    s3 = smooth_numbers(*n3d)
+    probs = []
+    while len(probs) < count:
+        dims = 2 if r.random() < 0.5 else 3
+        pool = s2 if dims == 2 else s3
+        n = tuple(int(pool[r.integers(len(pool))]) for _ in range(dims))
+        if max_points is not None and int(np.prod(n)) > max_points:
+            continue
+        bcs = tuple(int(r.integers(5)) for _ in range(dims))
+        probs.append(dict(dims=dims, n=n, bcs=bcs, Ls=(1.0,) * dims, gseed=int(r.integers(1 << 31))))
+    return probs
+
 
 def make_input(name_or_spec, shape=None, dtype=None):
     """Seeded right-hand side g for a workload (numpy array, shape (nz,ny,nx))."""
