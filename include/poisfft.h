@@ -192,6 +192,32 @@ int poisfft_batch_solve_sequential(poisfft_batch* batch, void* const phi[], cons
 int poisfft_batch_check(poisfft_batch* batch, void* stream);
 int poisfft_batch_destroy(poisfft_batch* batch);
 
+/* ---- FFT-preconditioned CG for div(a grad phi) = g (Sec. 1: the fast solve
+ * as a preconditioner for non-constant coefficients) ----
+ * Grid: n[3] cells on [0,L0]x[0,L1]x[0,L2], x fastest, cell-centred, phi = 0
+ * on every wall (staggered Dirichlet).  Operator: second-order fluxes with
+ * harmonic-mean face coefficients 2 a_i a_j / (a_i + a_j); a wall face uses
+ * the cell's a and the ghost value -phi.  For constant a it is a times the
+ * Table 4 staggered-Dirichlet FD2 Laplacian.
+ * poisfft_pcg_create: a = cell coefficients (n0*n1*n2 floats, host or device,
+ *   copied); a_ref > 0 is the preconditioner's constant coefficient, a_ref
+ *   <= 0 selects the mean of a.  The preconditioner is an FP32
+ *   poisfft_solve with staggered Dirichlet on every face.
+ * poisfft_pcg_solve: phi (device doubles) holds the initial guess on entry
+ *   and the solution on return; g (device doubles) the right-hand side.
+ *   Flexible PCG in FP64 (vectors, operator, inner products) until
+ *   ||g - A phi|| <= tol ||g|| or maxit iterations; *iters and *relres
+ *   report what was reached.  Synchronises `stream` every iteration (the
+ *   scalars of CG are read on the host).
+ * poisfft_pcg_apply: out = -(A in) (device doubles), the operator alone.
+ * No paper counterpart for the discretisation; it is this library's reading. */
+typedef struct poisfft_pcg poisfft_pcg;
+int poisfft_pcg_create(poisfft_pcg** out, const int64_t n[3], const double L[3], const float* a, double a_ref);
+int poisfft_pcg_solve(poisfft_pcg* pcg, double* phi, const double* g, double tol, int maxit, int* iters,
+                      double* relres, void* stream);
+int poisfft_pcg_apply(poisfft_pcg* pcg, double* out, const double* in, void* stream);
+int poisfft_pcg_destroy(poisfft_pcg* pcg);
+
 /* Per-launch timing for benchmarks (no paper counterpart; measurement aid).
  * When enabled, every solve records a CUDA event on its stream before each
  * kernel launch and after the last one.  Host cost: one event record per

@@ -50,6 +50,10 @@ EXPORTED = [
     "poisfft_batch_solve_sequential",
     "poisfft_batch_check",
     "poisfft_batch_destroy",
+    "poisfft_pcg_create",
+    "poisfft_pcg_solve",
+    "poisfft_pcg_apply",
+    "poisfft_pcg_destroy",
 ]
 
 
@@ -109,6 +113,17 @@ def _load():
     lib.poisfft_batch_check.restype = ctypes.c_int
     lib.poisfft_batch_destroy.argtypes = [ctypes.c_void_p]
     lib.poisfft_batch_destroy.restype = ctypes.c_int
+    lib.poisfft_pcg_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), i64p, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.c_void_p, ctypes.c_double]
+    lib.poisfft_pcg_create.restype = ctypes.c_int
+    lib.poisfft_pcg_solve.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                      ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.c_void_p]
+    lib.poisfft_pcg_solve.restype = ctypes.c_int
+    lib.poisfft_pcg_apply.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.poisfft_pcg_apply.restype = ctypes.c_int
+    lib.poisfft_pcg_destroy.argtypes = [ctypes.c_void_p]
+    lib.poisfft_pcg_destroy.restype = ctypes.c_int
     return lib
 
 
@@ -328,6 +343,55 @@ class Batch:
         if self._b:
             lib.poisfft_batch_destroy(self._b)
             self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class PCG:
+    """FFT-preconditioned CG for div(a grad phi) = g (staggered Dirichlet walls).
+
+    n, L: cells and lengths (x first); a: float32 cell coefficients (tensor or
+    address, n[2] x n[1] x n[0] x-fastest); a_ref <= 0 uses the mean of a."""
+
+    def __init__(self, n, L, a, a_ref=0.0):
+        h = ctypes.c_void_p()
+        n_arr = (ctypes.c_int64 * 3)(*[int(v) for v in n])
+        L_arr = (ctypes.c_double * 3)(*[float(v) for v in L])
+        rc = lib.poisfft_pcg_create(ctypes.byref(h), n_arr, L_arr, _ptr(a), float(a_ref))
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_pcg_create")
+        self._h = h
+
+    def solve(self, phi, g, tol=1e-8, maxit=500, stream=None):
+        """phi: initial guess in, solution out (float64 device).  Returns (iterations, relres)."""
+        it = ctypes.c_int()
+        rel = ctypes.c_double()
+        rc = lib.poisfft_pcg_solve(self._h, _ptr(phi), _ptr(g), float(tol), int(maxit), ctypes.byref(it),
+                                   ctypes.byref(rel), _stream(stream))
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_pcg_solve")
+        return it.value, rel.value
+
+    def apply(self, out, x, stream=None):
+        """out = -(A x)."""
+        rc = lib.poisfft_pcg_apply(self._h, _ptr(out), _ptr(x), _stream(stream))
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_pcg_apply")
+
+    def close(self):
+        if self._h:
+            lib.poisfft_pcg_destroy(self._h)
+            self._h = None
 
     def __del__(self):
         try:

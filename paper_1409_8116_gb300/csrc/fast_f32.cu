@@ -29,12 +29,13 @@ cudaError_t run_strided_mk(int mode, int kind, const CUtensorMap& map, const fas
   }
   if (mode == FM_FWD) return run_strided<R1, R2, W, FM_FWD, FK_DCT>(map, a, grid, smem, s);
   if (mode == FM_INV) return run_strided<R1, R2, W, FM_INV, FK_DCT>(map, a, grid, smem, s);
+  if (kind == FK_DCT_PAIR) return run_strided<R1, R2, W, FM_FUSED, FK_DCT_PAIR>(map, a, grid, smem, s);
   return run_strided<R1, R2, W, FM_FUSED, FK_DCT>(map, a, grid, smem, s);
 }
 
-template <int R1, int R2, int MODE>
+template <int R1, int R2, int MODE, int KX>
 cudaError_t run_x(const fast::FastXArgs& a, unsigned grid, size_t smem, cudaStream_t s) {
-  auto k = fast::fast_x_kernel<R1, R2, MODE>;
+  auto k = fast::fast_x_kernel<R1, R2, MODE, KX>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
@@ -44,8 +45,11 @@ cudaError_t run_x(const fast::FastXArgs& a, unsigned grid, size_t smem, cudaStre
 }
 
 template <int R1, int R2>
-cudaError_t run_x_m(int mode, const fast::FastXArgs& a, unsigned grid, size_t smem, cudaStream_t s) {
-  return mode == fast::FM_FWD ? run_x<R1, R2, fast::FM_FWD>(a, grid, smem, s) : run_x<R1, R2, fast::FM_INV>(a, grid, smem, s);
+cudaError_t run_x_m(int mode, int kx, const fast::FastXArgs& a, unsigned grid, size_t smem, cudaStream_t s) {
+  using namespace fast;
+  if (kx == FX_DCT)
+    return mode == FM_FWD ? run_x<R1, R2, FM_FWD, FX_DCT>(a, grid, smem, s) : run_x<R1, R2, FM_INV, FX_DCT>(a, grid, smem, s);
+  return mode == FM_FWD ? run_x<R1, R2, FM_FWD, FX_R2C>(a, grid, smem, s) : run_x<R1, R2, FM_INV, FX_R2C>(a, grid, smem, s);
 }
 
 }  // namespace
@@ -74,13 +78,14 @@ cudaError_t launch_fast_strided(int M, int W, int mode, int kind, const CUtensor
   }
 }
 
-cudaError_t launch_fast_x(int M, int mode, const fast::FastXArgs& a, unsigned grid, size_t smem, cudaStream_t s) {
+cudaError_t launch_fast_x(int M, int mode, int kx, const fast::FastXArgs& a, unsigned grid, size_t smem,
+                          cudaStream_t s) {
   switch (M) {
-    case 64: return run_x_m<8, 8>(mode, a, grid, smem, s);
-    case 128: return run_x_m<16, 8>(mode, a, grid, smem, s);
-    case 256: return run_x_m<16, 16>(mode, a, grid, smem, s);
-    case 512: return run_x_m<32, 16>(mode, a, grid, smem, s);
-    case 1024: return run_x_m<32, 32>(mode, a, grid, smem, s);
+    case 64: return run_x_m<8, 8>(mode, kx, a, grid, smem, s);
+    case 128: return run_x_m<16, 8>(mode, kx, a, grid, smem, s);
+    case 256: return run_x_m<16, 16>(mode, kx, a, grid, smem, s);
+    case 512: return run_x_m<32, 16>(mode, kx, a, grid, smem, s);
+    case 1024: return run_x_m<32, 32>(mode, kx, a, grid, smem, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -33,14 +33,20 @@
 namespace pf {
 namespace fast {
 
-enum FastKind : int { FK_DFT = 0, FK_DCT = 1 };
+// FK_DCT_PAIR: DCT axis whose complex columns pack two real x columns
+// (x itself DCT-II / DST-II); only the fused sweep differs (per-part divide).
+enum FastKind : int { FK_DFT = 0, FK_DCT = 1, FK_DCT_PAIR = 2 };
+// x transform of the contiguous sweep: real-to-complex DFT (periodic x) or
+// DCT-II / DST-II by the reordering of Makhoul (Neumann / Dirichlet
+// staggered x).
+enum FastXKind : int { FX_R2C = 0, FX_DCT = 1 };
 enum FastMode : int { FM_FWD = 0, FM_INV = 1, FM_FUSED = 2 };
 
 struct FastStridedArgs {
   const float2* tw;        // tw[s * R2 + j] = exp(-2 pi i j s / M), s < R1, j < R2
   const float2* mk;        // exp(-i pi k / (2M)), k < M (DCT axes)
   const float4* pk;        // fused DCT axes: (lam_ax[k], lam_ax[(M-k) mod M], cos(pi k/M), sin(pi k/M))
-  const float* lam_in;     // x eigenvalues by column
+  const float* lam_in;     // x eigenvalues by column (FK_DCT_PAIR: by real x index, 2 per column)
   const float* lam_ax;     // swept-axis eigenvalues in storage order
   const float* lam_out;    // outer-axis eigenvalues in storage order
   float scale;
@@ -56,6 +62,8 @@ struct FastStridedArgs {
 
 struct FastXArgs {
   const float2* tw;        // as above for the x line
+  const float2* mk;        // FX_DCT: exp(-i pi k / (2M)), k < M
+  int xsign;               // FX_DCT: 1 for DST-II / DST-III (Dirichlet staggered x)
   int nx;                  // = M
   int lines;               // line pairs per CTA
   long long nrows;         // ny * nz
@@ -98,7 +106,8 @@ template <int R1, int R2, int W, int MODE, int KIND>
 __global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, StridedMinBlocks<MODE, W * Shape<R1, R2>::RMAX>::value)
     fast_strided_kernel(const __grid_constant__ CUtensorMap tmap, const FastStridedArgs a) {
   constexpr int M = R1 * R2;
-  constexpr int NT = W * Shape<R1, R2>::RMAX;
+  constexpr bool DCT = KIND != FK_DFT;
+  constexpr bool PAIR = KIND == FK_DCT_PAIR;
   constexpr int BS = R2 * W + BlockPad<W>::value;  // padded block stride (complex)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
@@ -168,7 +177,7 @@ __global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, StridedMinBlocks<MODE
       Dft<float, R2, false>::run(y);
     }
 
-    if (KIND == FK_DCT) {
+    if (DCT) {
       // DCT-II post-processing needs Y_{M-k}: exchange through smem
       if (act2) {
 #pragma unroll
@@ -183,7 +192,7 @@ __global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, StridedMinBlocks<MODE
         for (int s2 = 0; s2 < R2; s2++) {
           const int k = b + R1 * s2;
           float2 x = y[s2];
-          if (KIND == FK_DCT) {
+          if (DCT) {
             const int kp = k == 0 ? 0 : M - k;
             const float2 yp = sm[(kp % R1) * BS + (kp / R1) * W + c];
             const float2 w = __ldg(&a.mk[k]);
@@ -198,7 +207,11 @@ __global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, StridedMinBlocks<MODE
     // ---- fused: divide by the eigenvalues, then DIT pass A in registers
     if (act2) {
       const int col = c0 + c;
-      const float lam_xo = (col < a.ncols ? __ldg(&a.lam_in[col]) : 0.f) + __ldg(&a.lam_out[outer]);
+      const float lam_o = __ldg(&a.lam_out[outer]);
+      const float lam_xo = PAIR ? 0.f : (col < a.ncols ? __ldg(&a.lam_in[col]) : 0.f) + lam_o;
+      // PAIR: the real and imaginary parts are x columns 2 col and 2 col + 1
+      const float lam_xo0 = PAIR ? (col < a.ncols ? __ldg(&a.lam_in[2 * col]) : 0.f) + lam_o : 0.f;
+      const float lam_xo1 = PAIR ? (col < a.ncols ? __ldg(&a.lam_in[2 * col + 1]) : 0.f) + lam_o : 0.f;
       const bool zero_row = a.singular && col == 0 && outer == 0;
 #pragma unroll
       for (int s2 = 0; s2 < R2; s2++) {
@@ -207,6 +220,29 @@ __global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, StridedMinBlocks<MODE
           float f = __fdividef(a.scale, lam_xo + __ldg(&a.lam_ax[k]));
           if (zero_row && k == 0) f = 0.f;
           y[s2] = make_float2(y[s2].x * f, y[s2].y * f);
+        } else if (PAIR) {
+          // The column packs two real sequences: Y = Yu + i Yv with Yu, Yv
+          // Hermitian (Yu_k = (Y_k + conj(Y_{M-k})) / 2, Yv_k = (Y_k -
+          // conj(Y_{M-k})) / 2i); each part takes the step below with its own
+          // x eigenvalue, using Y*_{M-k} = conj(Y*_k).
+          const int prow = b == 0 ? (R2 - s2) % R2 : R2 - 1 - s2;
+          const float2 yp = sm[((R1 - b) % R1) * BS + prow * W + c];
+          const float2 yk = y[s2];
+          const float2 Yu = make_float2(0.5f * (yk.x + yp.x), 0.5f * (yk.y - yp.y));
+          const float2 Yv = make_float2(0.5f * (yk.y + yp.y), 0.5f * (yp.x - yk.x));
+          const float4 t = __ldg(&a.pk[k]);
+          float f0k = __fdividef(a.scale, lam_xo0 + t.x);
+          float f0m = k == 0 ? f0k : __fdividef(a.scale, lam_xo0 + t.y);
+          if (zero_row && k == 0) f0k = f0m = 0.f;
+          const float f1k = __fdividef(a.scale, lam_xo1 + t.x);
+          const float f1m = k == 0 ? f1k : __fdividef(a.scale, lam_xo1 + t.y);
+          // e^{i pi k / M} conj(Y)
+          const float2 cu = make_float2(t.z * Yu.x + t.w * Yu.y, t.w * Yu.x - t.z * Yu.y);
+          const float2 cv = make_float2(t.z * Yv.x + t.w * Yv.y, t.w * Yv.x - t.z * Yv.y);
+          const float al0 = f0k + f0m, be0 = f0k - f0m, al1 = f1k + f1m, be1 = f1k - f1m;
+          const float2 Vu = make_float2(al0 * Yu.x + be0 * cu.x, al0 * Yu.y + be0 * cu.y);
+          const float2 Vv = make_float2(al1 * Yv.x + be1 * cv.x, al1 * Yv.y + be1 * cv.y);
+          y[s2] = make_float2(Vu.x - Vv.y, Vu.y + Vv.x);
         } else {
           // DCT-II post, divide and DCT-III pre in one step: with
           // X_k = w Y_k + conj(w) Y_{M-k}, X_{M-k} = i (w Y_k - conj(w) Y_{M-k}),
@@ -226,7 +262,7 @@ __global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, StridedMinBlocks<MODE
       }
       Dft<float, R2, true>::run(y);
     }
-    if (KIND == FK_DCT) __syncthreads();  // partners have read this block
+    if (DCT) __syncthreads();  // partners have read this block
     if (act2) {
 #pragma unroll
       for (int s = 0; s < R2; s++) sm[b * BS + s * W + c] = y[s];
@@ -242,7 +278,7 @@ __global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, StridedMinBlocks<MODE
       for (int q = 0; q < R2; q++) {
         const int k = b + R1 * q;
         float2 x = sm[k * W + c];
-        if (KIND == FK_DCT) {
+        if (DCT) {
           // V_k = conj(w_k) (X_k - i X_{M-k}), X_M = 0
           const float2 xm = k == 0 ? make_float2(0.f, 0.f) : sm[(M - k) * W + c];
           x = cmulc<float>(make_float2(x.x + xm.y, x.y - xm.x), __ldg(&a.mk[k]));
@@ -298,7 +334,18 @@ __device__ __forceinline__ void ws_row_of(const FastXArgs& a, long long r, long 
   wr = (long long)z * a.ny + y;
 }
 
-template <int R1, int R2, int MODE>
+// FX_DCT: two real rows a, b form one complex line.  Forward: the line
+// holds v_m = x_{2m} (m < M/2), v_m = x_{2M-1-2m} (m >= M/2), times -1 on the
+// odd samples for DST-II; after the FFT Z = V_a + i V_b, and
+//   X_a,k = Re(w_k Z_k) + Re(w_k conj(Z_{M-k})),
+//   X_b,k = Im(w_k Z_k) - Im(w_k conj(Z_{M-k})),  w_k = exp(-i pi k / 2M),
+// the DCT-II (2 sum x_n cos(pi k (2n+1) / 2M)) of each row, stored as M
+// reals per workspace row (two x coefficients per complex column).
+// Backward: V_k = conj(w_k) (X_k - i X_{M-k}), V_{M-k} = w_k (X_k + i X_{M-k})
+// (X_M = 0) for each row, Z = V_a + i V_b, inverse FFT, and the samples go
+// back to x_{2m} / x_{2M-1-2m} (DCT-III; DST-III with the odd samples
+// negated).
+template <int R1, int R2, int MODE, int KX>
 __global__ void __launch_bounds__(256, MODE == 0 ? 2 : 3) fast_x_kernel(const FastXArgs a) {
   constexpr int M = R1 * R2;
   constexpr int RMAX = Shape<R1, R2>::RMAX;
@@ -326,7 +373,17 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 2 : 3) fast_x_kernel(const Fa
       const float* ga = a.g + (ra % a.ny) * a.g_sy + (ra / a.ny) * a.g_sz;
       const float* gb = a.g + (rb % a.ny) * a.g_sy + (rb / a.ny) * a.g_sz;
 #pragma unroll
-      for (int q = 0; q < R1; q++) u[q] = make_float2(va ? ga[j + R2 * q] : 0.f, vb ? gb[j + R2 * q] : 0.f);
+      for (int q = 0; q < R1; q++) {
+        const int m = j + R2 * q;
+        if (KX == FX_R2C) {
+          u[q] = make_float2(va ? ga[m] : 0.f, vb ? gb[m] : 0.f);
+        } else {
+          const bool odd = q >= R1 / 2;  // m >= M/2
+          const int src = odd ? 2 * M - 1 - 2 * m : 2 * m;
+          const float sg = (odd && a.xsign) ? -1.f : 1.f;
+          u[q] = make_float2(va ? sg * ga[src] : 0.f, vb ? sg * gb[src] : 0.f);
+        }
+      }
       Dft<float, R1, false>::run(u);
       if (j != 0) {
 #pragma unroll
@@ -346,42 +403,82 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 2 : 3) fast_x_kernel(const Fa
       for (int s = 0; s < R2; s++) line[b * (R2 + 1) + s] = y[s];
     }
     __syncthreads();
-    // split Z into the half spectra of rows a and b
-    constexpr int NH = M / 2 + 1;
-    float2* da = a.ws + wa * a.ws_ld;
-    float2* db = a.ws + wb * a.ws_ld;
-    for (int k = bi; k < NH; k += RMAX) {
-      const float2 z1 = line[xpos<R1, R2>(k)];
-      const float2 z2 = line[xpos<R1, R2>(k == 0 ? 0 : M - k)];
-      const float2 A = make_float2(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y));
-      const float2 B = make_float2(0.5f * (z1.y + z2.y), 0.5f * (z2.x - z1.x));
-      if (va) da[k] = make_float2(sa * A.x, sa * A.y);
-      if (vb) db[k] = make_float2(sb * B.x, sb * B.y);
+    if (KX == FX_R2C) {
+      // split Z into the half spectra of rows a and b
+      constexpr int NH = M / 2 + 1;
+      float2* da = a.ws + wa * a.ws_ld;
+      float2* db = a.ws + wb * a.ws_ld;
+      for (int k = bi; k < NH; k += RMAX) {
+        const float2 z1 = line[xpos<R1, R2>(k)];
+        const float2 z2 = line[xpos<R1, R2>(k == 0 ? 0 : M - k)];
+        const float2 A = make_float2(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y));
+        const float2 B = make_float2(0.5f * (z1.y + z2.y), 0.5f * (z2.x - z1.x));
+        if (va) da[k] = make_float2(sa * A.x, sa * A.y);
+        if (vb) db[k] = make_float2(sb * B.x, sb * B.y);
+      }
+    } else {
+      float* da = reinterpret_cast<float*>(a.ws + wa * a.ws_ld);
+      float* db = reinterpret_cast<float*>(a.ws + wb * a.ws_ld);
+      for (int k = bi; k < M; k += RMAX) {
+        const float2 z1 = line[xpos<R1, R2>(k)];
+        const float2 z2 = line[xpos<R1, R2>(k == 0 ? 0 : M - k)];
+        const float2 w = __ldg(&a.mk[k]);
+        const float2 p1 = cmul<float>(w, z1);
+        const float2 p2 = cmul<float>(w, make_float2(z2.x, -z2.y));
+        if (va) da[k] = sa * (p1.x + p2.x);
+        if (vb) db[k] = sb * (p1.y - p2.y);
+      }
     }
   } else {
-    // C2R assembly into the digit-reversed arrangement (all loads first)
     constexpr int NH = M / 2 + 1;
     constexpr int NK = (NH + RMAX - 1) / RMAX;
-    const float2* sa_p = a.ws + wa * a.ws_ld;
-    const float2* sb_p = a.ws + wb * a.ws_ld;
-    float2 Av[NK], Bv[NK];
+    if (KX == FX_R2C) {
+      // C2R assembly into the digit-reversed arrangement (all loads first)
+      const float2* sa_p = a.ws + wa * a.ws_ld;
+      const float2* sb_p = a.ws + wb * a.ws_ld;
+      float2 Av[NK], Bv[NK];
 #pragma unroll
-    for (int i = 0; i < NK; i++) {
-      const int k = bi + i * RMAX;
-      Av[i] = (va && k < NH) ? sa_p[k] : make_float2(0.f, 0.f);
-      Bv[i] = (vb && k < NH) ? sb_p[k] : make_float2(0.f, 0.f);
-    }
+      for (int i = 0; i < NK; i++) {
+        const int k = bi + i * RMAX;
+        Av[i] = (va && k < NH) ? sa_p[k] : make_float2(0.f, 0.f);
+        Bv[i] = (vb && k < NH) ? sb_p[k] : make_float2(0.f, 0.f);
+      }
 #pragma unroll
-    for (int i = 0; i < NK; i++) {
-      const int k = bi + i * RMAX;
-      if (k >= NH) break;
-      const float2 A = make_float2(sa * Av[i].x, sa * Av[i].y);
-      const float2 B = make_float2(sb * Bv[i].x, sb * Bv[i].y);
-      if (k == 0 || 2 * k == M) {
-        line[xpos<R1, R2>(k)] = make_float2(A.x, B.x);
-      } else {
-        line[xpos<R1, R2>(k)] = make_float2(A.x - B.y, A.y + B.x);
-        line[xpos<R1, R2>(M - k)] = make_float2(A.x + B.y, B.x - A.y);
+      for (int i = 0; i < NK; i++) {
+        const int k = bi + i * RMAX;
+        if (k >= NH) break;
+        const float2 A = make_float2(sa * Av[i].x, sa * Av[i].y);
+        const float2 B = make_float2(sb * Bv[i].x, sb * Bv[i].y);
+        if (k == 0 || 2 * k == M) {
+          line[xpos<R1, R2>(k)] = make_float2(A.x, B.x);
+        } else {
+          line[xpos<R1, R2>(k)] = make_float2(A.x - B.y, A.y + B.x);
+          line[xpos<R1, R2>(M - k)] = make_float2(A.x + B.y, B.x - A.y);
+        }
+      }
+    } else {
+      // DCT-III pre-processing of rows a, b for k and M - k (all loads first)
+      const float* sa_p = reinterpret_cast<const float*>(a.ws + wa * a.ws_ld);
+      const float* sb_p = reinterpret_cast<const float*>(a.ws + wb * a.ws_ld);
+      float xa[NK], xam[NK], xb[NK], xbm[NK];
+#pragma unroll
+      for (int i = 0; i < NK; i++) {
+        const int k = bi + i * RMAX;
+        const bool in = k < NH;
+        xa[i] = (va && in) ? sa * sa_p[k] : 0.f;
+        xb[i] = (vb && in) ? sb * sb_p[k] : 0.f;
+        xam[i] = (va && in && k > 0) ? sa * sa_p[M - k] : 0.f;
+        xbm[i] = (vb && in && k > 0) ? sb * sb_p[M - k] : 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < NK; i++) {
+        const int k = bi + i * RMAX;
+        if (k >= NH) break;
+        const float2 w = __ldg(&a.mk[k]);
+        // Z_k = conj(w) ((xa + xbm) + i (xb - xam)), Z_{M-k} = w ((xa - xbm) + i (xb + xam))
+        line[xpos<R1, R2>(k)] = cmulc<float>(make_float2(xa[i] + xbm[i], xb[i] - xam[i]), w);
+        if (k != 0 && 2 * k != M)
+          line[xpos<R1, R2>(M - k)] = cmul<float>(w, make_float2(xa[i] - xbm[i], xb[i] + xam[i]));
       }
     }
     __syncthreads();
@@ -409,8 +506,17 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 2 : 3) fast_x_kernel(const Fa
       float* pb = a.phi + (rb % a.ny) * a.phi_sy + (rb / a.ny) * a.phi_sz;
 #pragma unroll
       for (int s = 0; s < R1; s++) {
-        if (va) pa[j + R2 * s] = u[s].x;
-        if (vb) pb[j + R2 * s] = u[s].y;
+        const int n = j + R2 * s;
+        if (KX == FX_R2C) {
+          if (va) pa[n] = u[s].x;
+          if (vb) pb[n] = u[s].y;
+        } else {
+          const bool odd = s >= R1 / 2;  // n >= M/2
+          const int dst = odd ? 2 * M - 1 - 2 * n : 2 * n;
+          const float sg = (odd && a.xsign) ? -1.f : 1.f;
+          if (va) pa[dst] = sg * u[s].x;
+          if (vb) pb[dst] = sg * u[s].y;
+        }
       }
     }
   }

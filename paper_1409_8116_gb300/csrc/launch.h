@@ -30,6 +30,7 @@ cudaError_t launch_pair_divide(const PairDivideArgs& a, cudaStream_t s);
 bool fast_shape(int M, int* R1, int* R2, int* W);
 cudaError_t launch_fast_strided(int M, int W, int mode, int kind, const CUtensorMap& map,
                                 const fast::FastStridedArgs& a, unsigned grid, size_t smem, cudaStream_t s);
-cudaError_t launch_fast_x(int M, int mode, const fast::FastXArgs& a, unsigned grid, size_t smem, cudaStream_t s);
+cudaError_t launch_fast_x(int M, int mode, int kx, const fast::FastXArgs& a, unsigned grid, size_t smem,
+                          cudaStream_t s);
 
 }  // namespace pf

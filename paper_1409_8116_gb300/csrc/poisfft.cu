@@ -533,22 +533,25 @@ int plan_strided_sweep(poisfft_plan* p, int axis, int mode, SweepLaunch& L) {
 }
 
 // ---------------------------------------------------------------------------
-// specialised path: every axis two-pass FP32, x periodic, y/z P, NS or DS
+// specialised path: every axis two-pass FP32; x periodic with y/z P, NS or
+// DS, or x NS / DS with y/z NS or DS
 // ---------------------------------------------------------------------------
+bool dct_axis(const AxisPlan& ax) { return ax.bc == POISFFT_NS || ax.bc == POISFFT_DS; }
+
 bool fast_eligible(const poisfft_plan* p) {
-  if (p->esize != 4 || p->dims < 2 || !p->r2c) return false;
+  if (p->esize != 4 || p->dims < 2) return false;
   const char* env = getenv("POISFFT_FORCE_GENERIC");
   if (env && env[0] && env[0] != '0') return false;
+  const bool xdct = dct_axis(p->axes[0]);
+  if (!p->r2c && !xdct) return false;
   int r1, r2, w;
   for (int a = 0; a < p->dims; a++) {
     if (!fast_shape(p->axes[a].n, &r1, &r2, &w)) return false;
     const int bc = p->axes[a].bc;
-    if (a == 0 ? bc != POISFFT_P : !(bc == POISFFT_P || bc == POISFFT_NS || bc == POISFFT_DS)) return false;
+    if (a > 0 && !(bc == POISFFT_NS || bc == POISFFT_DS || (bc == POISFFT_P && !xdct))) return false;
   }
   return true;
 }
-
-bool dct_axis(const AxisPlan& ax) { return ax.bc == POISFFT_NS || ax.bc == POISFFT_DS; }
 
 // Tables of one axis for the specialised kernels, FP64 -> float:
 //   tw[s*R2 + j] = exp(-2 pi i j s / M);  mk[k] = exp(-i pi k/(2M));
@@ -615,6 +618,8 @@ void plan_fast_x(poisfft_plan* p, int mode, SweepLaunch& L) {
   a.sign_y = p->dims >= 2 && p->axes[1].bc == POISFFT_DS;
   a.sign_z = p->dims >= 3 && p->axes[2].bc == POISFFT_DS;
   a.ws_ld = p->pitch;
+  L.fkind = p->r2c ? fast::FX_R2C : fast::FX_DCT;
+  a.xsign = p->axes[0].bc == POISFFT_DS;
   const long long pairs = (a.nrows + 1) / 2;
   L.grid = (unsigned)((pairs + lpc - 1) / lpc);
   L.smem = (size_t)lpc * R1 * (R2 + 1) * 8;
@@ -632,6 +637,7 @@ void plan_fast_strided(poisfft_plan* p, int axis, int mode, SweepLaunch& L) {
   L.M = M;
   L.fmode = mode;
   L.fkind = dct_axis(ax) ? fast::FK_DCT : fast::FK_DFT;
+  if (mode == fast::FM_FUSED && !p->r2c) L.fkind = fast::FK_DCT_PAIR;  // x DCT-II / DST-II columns
   L.axis = axis;
   L.w = W;
   L.box_h = std::min(M, 256);
@@ -659,6 +665,7 @@ void patch_fast(poisfft_plan* p) {
   for (auto& L : p->sweeps) {
     if (L.kind == 2) {
       L.fxa.tw = static_cast<const float2*>(p->ftw[0]);
+      L.fxa.mk = static_cast<const float2*>(p->fmk[0]);
       L.fxa.ws = static_cast<float2*>(p->ws);
     } else if (L.kind == 3) {
       const int a = L.axis;
@@ -666,7 +673,7 @@ void patch_fast(poisfft_plan* p) {
       s.tw = static_cast<const float2*>(p->ftw[a]);
       s.mk = static_cast<const float2*>(p->fmk[a]);
       s.pk = static_cast<const float4*>(p->fpk[a]);
-      s.lam_in = static_cast<const float*>(p->lam[0]);
+      s.lam_in = static_cast<const float*>(L.fkind == fast::FK_DCT_PAIR ? p->flam[0] : p->lam[0]);
       s.lam_ax = static_cast<const float*>(p->flam[a]);
       s.lam_out = static_cast<const float*>(a == 1 ? (p->dims >= 3 ? p->flam[2] : p->lam[2]) : p->flam[1]);
       s.data = static_cast<float2*>(p->ws);
@@ -741,7 +748,7 @@ int enqueue(poisfft_plan* p, void* phi, const void* g, cudaStream_t st, const Fi
       a.g_sz = fs.g_sz;
       a.phi_sy = fs.phi_sy;
       a.phi_sz = fs.phi_sz;
-      e = launch_fast_x(L.M, L.fmode, a, L.grid, L.smem, st);
+      e = launch_fast_x(L.M, L.fmode, L.fkind, a, L.grid, L.smem, st);
     } else {
       e = launch_fast_strided(L.M, L.w, L.fmode, L.fkind, p->maps[L.map], L.fsa, L.grid, L.smem, st);
     }

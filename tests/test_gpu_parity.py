@@ -222,8 +222,9 @@ def test_misaligned_pointer_rejected(pb):
 
 
 # ---------------------------------------------------------------------------
-# specialised two-pass kernels (x periodic, y/z in {P, NS, DS}, lengths
-# 64...1024) and the generic kernels on the same shapes
+# specialised two-pass kernels (x periodic with y/z in {P, NS, DS}, or x, y,
+# z all in {NS, DS}; lengths 64...1024) and the generic kernels on the same
+# shapes
 # ---------------------------------------------------------------------------
 
 FAST3 = [(64, 64, 64), (128, 64, 256), (1024, 64, 64), (512, 256, 64), (64, 128, 1024), (256, 1024, 64)]
@@ -245,9 +246,31 @@ def test_fast_path_2d(pb, n, bcs):
     check(pb, tuple(reversed(n)), bcs, W.SPECTRAL, "f32", seed=13, method="fft")
 
 
-def test_fast_and_generic_kernels_agree(pb, monkeypatch):
+# x Neumann / Dirichlet staggered (DCT-II / DST-II x sweep by Makhoul's
+# reordering, two x columns per complex workspace column) with y, z NS / DS
+FAST3_X = [(64, 64, 64), (256, 128, 64), (128, 64, 512), (1024, 64, 64)]
+FAST_X_BCS = list(itertools.product([W.NS, W.DS], repeat=3))
+
+
+@pytest.mark.parametrize("n", FAST3_X, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("bcs", FAST_X_BCS, ids=lambda b: "".join(O.BC_NAMES[x] for x in b))
+def test_fast_path_3d_x_cosine_sine(pb, n, bcs):
+    shape = tuple(reversed(n))
+    method = "dense" if np.prod(n) <= 1 << 20 else "fft"
+    check(pb, shape, bcs, W.FD2, "f32", seed=15, method=method)
+
+
+@pytest.mark.parametrize("n,bcs,approx", [((256, 512), (W.NS, W.DS), W.SPECTRAL), ((1024, 64), (W.DS, W.NS), W.FD2),
+                                          ((64, 64), (W.NS, W.NS), W.FD2), ((512, 128), (W.DS, W.DS), W.SPECTRAL)])
+def test_fast_path_2d_x_cosine_sine(pb, n, bcs, approx):
+    check(pb, tuple(reversed(n)), bcs, approx, "f32", seed=16, method="fft")
+
+
+@pytest.mark.parametrize("bcs", [(W.P, W.DS, W.NS), (W.NS, W.DS, W.NS), (W.DS, W.DS, W.DS)],
+                         ids=lambda b: "".join(O.BC_NAMES[x] for x in b))
+def test_fast_and_generic_kernels_agree(pb, monkeypatch, bcs):
     shape = (128, 64, 256)
-    bcs, Ls = (W.P, W.DS, W.NS), (1.0, 1.0, 1.0)
+    Ls = (1.0, 1.0, 1.0)
     g = W.normal(shape, 14, dtype=np.float32)
     fast = gpu_solve(pb, g, bcs, Ls, W.FD2, "f32")
     monkeypatch.setenv("POISFFT_FORCE_GENERIC", "1")

@@ -1,0 +1,127 @@
+"""FFT-preconditioned CG for div(a grad phi) = g (Sec. 1) on the GPU.
+
+* The operator alone (poisfft_pcg_apply) against the FP64 oracle, element by
+  element.
+* Solutions against the exact discrete solution (sparse LU of the oracle's
+  operator, extracted by 27-colour probing) and against the oracle's PCG
+  (same algorithm, FP64 preconditioner): iteration counts within 5 %,
+  solutions within the accuracy the tolerance implies.
+* Special cases: constant a (the preconditioner is exact up to FP32
+  rounding: a couple of iterations), g = 0, an initial guess that is already
+  the solution, the iteration cap.
+"""
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import vc_operator as V
+from tests._lib import ensure_built
+from tests._vc import sparse_operator as _sparse_operator
+
+torch = pytest.importorskip("torch")
+spla = pytest.importorskip("scipy.sparse.linalg")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ensure_built()
+    from paper_1409_8116_gb300 import binding
+    return binding
+
+
+def _problem(n, contrast, seed):
+    shape = tuple(reversed(n))
+    a = W.lognormal_coefficient(shape, seed, contrast)
+    g = W.normal(shape, seed + 1)
+    return a, g
+
+
+@pytest.mark.parametrize("n", [(37, 29, 23), (64, 64, 64), (1, 5, 300)])
+def test_apply_matches_oracle(pb, n):
+    a, _ = _problem(n, 100.0, 11)
+    x = W.normal(a.shape, 12)
+    Ls = (1.0, 1.3, 0.8)
+    ref = V.apply_operator(x, a.astype(np.float64), Ls)
+    with pb.PCG(n, Ls, torch.from_numpy(a).cuda()) as s:
+        xd = torch.from_numpy(x).cuda()
+        out = torch.full_like(xd, float("nan"))
+        s.apply(out, xd, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+    got = -out.cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("n,contrast,Ls", [
+    ((24, 20, 16), 100.0, (1.0, 1.0, 1.0)),
+    ((33, 17, 26), 10.0, (2.0, 1.0, 1.5)),
+])
+def test_solution_matches_exact_and_oracle_pcg(pb, n, contrast, Ls):
+    a, g = _problem(n, contrast, 21)
+    a64 = a.astype(np.float64)
+    A = _sparse_operator(a64, Ls)
+    exact = spla.splu(A).solve(g.ravel()).reshape(g.shape)
+    tol = 1e-11
+    ref, it_ref, rel_ref = V.pcg(g, a64, Ls, tol=tol, maxit=200)
+    with pb.PCG(n, Ls, torch.from_numpy(a).cuda()) as s:
+        gd = torch.from_numpy(g).cuda()
+        phi = torch.zeros_like(gd)
+        it, rel = s.solve(phi, gd, tol=tol, maxit=200, stream=torch.cuda.current_stream())
+        torch.cuda.synchronize()
+    phi = phi.cpu().numpy()
+    assert rel <= tol and it < 200
+    # the FP32 preconditioner perturbs the FP64 one by ~1e-7: a few more
+    # iterations at most at this tolerance
+    assert abs(it - it_ref) <= max(2, it_ref // 20), (it, it_ref)
+    true_rel = np.linalg.norm(g - V.apply_operator(phi, a64, Ls)) / np.linalg.norm(g)
+    assert true_rel <= 10 * tol
+    scale = np.max(np.abs(exact))
+    assert np.max(np.abs(phi - exact)) <= 1e-8 * scale
+    assert np.max(np.abs(phi - ref)) <= 1e-8 * scale
+
+
+def test_constant_coefficient_converges_in_few_iterations(pb):
+    n = (40, 30, 20)
+    a = np.full(tuple(reversed(n)), 2.5, np.float32)
+    g = W.normal(a.shape, 5)
+    with pb.PCG(n, (1.0, 1.0, 1.0), torch.from_numpy(a).cuda()) as s:
+        gd = torch.from_numpy(g).cuda()
+        phi = torch.zeros_like(gd)
+        it, rel = s.solve(phi, gd, tol=1e-10, maxit=50)
+    # the FP32 preconditioner is the exact inverse up to ~1e-7 relative
+    assert it <= 3 and rel <= 1e-10
+
+
+def test_special_cases(pb):
+    n = (16, 12, 10)
+    a, g = _problem(n, 30.0, 8)
+    Ls = (1.0, 1.0, 1.0)
+    with pb.PCG(n, Ls, torch.from_numpy(a).cuda(), a_ref=1.0) as s:
+        zero = torch.zeros(a.shape, dtype=torch.float64, device="cuda")
+        phi = torch.zeros_like(zero)
+        assert s.solve(phi, zero, tol=1e-10) == (0, 0.0)
+        assert torch.count_nonzero(phi) == 0
+        gd = torch.from_numpy(g).cuda()
+        it, rel = s.solve(phi, gd, tol=1e-12, maxit=300)
+        assert rel <= 1e-12
+        again = phi.clone()
+        it2, rel2 = s.solve(again, gd, tol=1e-6, maxit=300)   # start at the solution
+        assert it2 == 0 and rel2 <= 1e-6 and torch.equal(again, phi)
+        capped = torch.zeros_like(gd)
+        it3, rel3 = s.solve(capped, gd, tol=1e-14, maxit=3)
+        assert it3 == 3 and rel3 > 1e-14
+        # three iterations from zero are exactly the first three of the full run
+        first3 = torch.zeros_like(gd)
+        s.solve(first3, gd, tol=0.0, maxit=3)
+        assert torch.equal(first3, capped)
+
+
+def test_invalid_arguments(pb):
+    with pytest.raises(pb.PoisFFTError):
+        pb.PCG((0, 4, 4), (1.0, 1.0, 1.0), torch.ones(16, device="cuda"))
+    with pytest.raises(pb.PoisFFTError):
+        pb.PCG((4, 4, 4), (1.0, -1.0, 1.0), torch.ones(64, device="cuda"))

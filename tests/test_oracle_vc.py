@@ -77,3 +77,28 @@ def test_pcg_solves_discrete_equation_and_matches_dense(contrast):
     assert O.rel_max_error(phi.ravel(), x) < 1e-10
     if contrast == 1.0:
         assert it <= 2          # the preconditioner is the exact inverse
+
+
+def test_sparse_probe_reproduces_operator():
+    from tests._vc import sparse_operator
+    r = np.random.default_rng(4)
+    shape = (5, 6, 7)
+    a = np.exp(r.standard_normal(shape))
+    Ls = (1.0, 0.9, 1.1)
+    A = sparse_operator(a, Ls)
+    np.testing.assert_allclose(A.toarray(), _dense(shape, a, Ls), rtol=0, atol=1e-12 * np.abs(A).max())
+
+
+def test_pcg_matches_sparse_lu_on_a_larger_grid():
+    import scipy.sparse.linalg as spla
+    from tests._vc import sparse_operator
+    r = np.random.default_rng(5)
+    shape = (12, 14, 16)
+    s = r.standard_normal(shape)
+    a = 100.0 ** ((s - s.min()) / (s.max() - s.min()) - 0.5)
+    g = r.standard_normal(shape)
+    Ls = (1.5, 1.0, 0.75)
+    phi, it, rel = V.pcg(g, a, Ls, tol=1e-12, maxit=300)
+    x = spla.splu(sparse_operator(a, Ls)).solve(g.ravel())
+    assert rel <= 1e-12 and it < 300
+    assert O.rel_max_error(phi.ravel(), x) < 1e-9

@@ -126,6 +126,24 @@ BATCHES = {
 }
 
 
+# Variable-coefficient problems div(a grad phi) = g (staggered Dirichlet on
+# every wall) solved by CG preconditioned with the FD2 Poisson solve.
+VC_PROBLEMS = {
+    # 256^3 cells on the unit cube, a log-normal with max/min = 100
+    "pcg_vc_256_f64": dict(n=(256, 256, 256), Ls=(1.0, 1.0, 1.0), contrast=100.0, seed=5, tol=1e-8),
+}
+
+
+def lognormal_coefficient(shape, seed, contrast):
+    """Cell coefficients a = contrast ** (s / 2) with s a smooth Gaussian
+    random field (spectrum ~ |k|^-4) mapped affinely onto [-1, 1], so that
+    max(a) / min(a) = contrast and a spans [contrast^-1/2, contrast^1/2].
+    FP32 (the coefficient is stored in FP32 by the solver)."""
+    s = smooth_random_field(shape, seed, slope=-4.0, noise=0.0, dtype=np.float64)
+    s = 2.0 * (s - s.min()) / (s.max() - s.min()) - 1.0
+    return (float(contrast) ** (0.5 * s)).astype(np.float32)
+
+
 def smooth_numbers(lo, hi, primes=(2, 3, 5, 7)):
     """Integers in [lo, hi] whose prime factors all lie in `primes`."""
     out = []
