@@ -466,18 +466,21 @@ def run_batch(args):
 
 PCG_METRIC = "variable-coefficient PCG: cell-iterations/s (FFT preconditioner), time to tolerance"
 PCG_UNIT = "cell-iterations/s"
-# FP64 bytes per cell and iteration of the CG kernels around the
-# preconditioner (apply 20, update 52, precondition scaling 28, direction 24),
-# plus the FP32 Poisson solve (3 transform sweeps, read + write 4 B each, and
-# the scaling reads/writes of r32/z32 already counted above).
-PCG_BYTES_OWN = 124
-PCG_BYTES_POISSON = 24
+# Algorithmic bytes per cell and iteration of the mixed-precision iteration:
+# operator 20 (p, three FP32 face coefficients, q), update 24 (e and r read
+# and written, p, q), preconditioner inner products 12 (r and two
+# preconditioner outputs), direction 12 (output, p read and written), and
+# the FP32 Poisson solve as five sweeps that read and write 4 B each.
+PCG_BYTES_OWN = 68
+PCG_BYTES_POISSON = 40
 
 
 def run_pcg(args):
     """Variable-coefficient workload: one step = one PCG solve from phi = 0
-    to the workload's tolerance.  `value` counts cells x iterations per
-    second; the solve time and the iteration count are reported beside it."""
+    to the workload's tolerance (mixed precision: FP32 iterations, FP64
+    reliable updates; the FP64 iteration is timed beside it).  `value`
+    counts cells x iterations per second; the solve time and the iteration
+    count are reported beside it."""
     import torch
 
     from paper_1409_8116_gb300 import binding as pb
@@ -494,32 +497,36 @@ def run_pcg(args):
     phi = torch.zeros_like(g)
     solver = pb.PCG(n, spec["Ls"], a)
     torch.cuda.synchronize()
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            phi.zero_()
-            its, rel = solver.solve(phi, g, spec["tol"], 1000, stream)
+
+    def timed(precision, steps, warmup):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                phi.zero_()
+                solver.solve(phi, g, spec["tol"], 1000, stream, precision)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            iters = []
+            e0.record(stream)
+            for _ in range(steps):
+                phi.zero_()
+                its, rel = solver.solve(phi, g, spec["tol"], 1000, stream, precision)
+                iters.append(its)
+            e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1), iters, rel, solver.stats()
+
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    iters = []
-    with torch.cuda.stream(stream):
-        e0.record(stream)
-        for _ in range(args.steps):
-            phi.zero_()
-            its, rel = solver.solve(phi, g, spec["tol"], 1000, stream)
-            iters.append(its)
-        e1.record(stream)
-    stream.synchronize()
+    ms, iters, rel, stats = timed(pb.PCG_MIXED, args.steps, args.warmup)
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
+    sol = phi.cpu().numpy()
+    ms64, iters64, rel64, _ = timed(pb.PCG_F64, max(1, min(args.steps, 3)), 1)
     total_it = sum(iters)
     value = npts * total_it / (ms / 1e3)
     true_rel = None
     if not args.no_check:
         from oracle import vc_operator as V
 
-        sol = phi.cpu().numpy()
         true_rel = float(np.linalg.norm(g_host - V.apply_operator(sol, a_host.astype(np.float64), spec["Ls"]))
                          / np.linalg.norm(g_host))
     cpu = None
@@ -537,15 +544,19 @@ def run_pcg(args):
     peak, peak_kind = load_peaks()
     ms_it = ms / total_it
     achieved = npts * (PCG_BYTES_OWN + PCG_BYTES_POISSON) / (ms_it / 1e3) / 1e9
+    n64 = len(iters64)
     line = {
         "metric": PCG_METRIC, "value": value, "unit": PCG_UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64 (CG) + f32 (preconditioner)", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32 iterations + f64 reliable updates", "data": "synthetic",
         "config": {"workload": args.workload, "n": list(n), "contrast": spec["contrast"], "tol": spec["tol"],
                    "l2": "inputs larger than L2 (no flush needed)"},
         "iterations": iters[-1], "ms_per_iteration": ms_it, "relres": rel, "true_relres": true_rel,
+        "fp64_true_residuals": stats["true_residuals"],
+        "f64_iteration": {"ms_per_solve": ms64 / n64, "iterations": iters64[-1], "relres": rel64,
+                          "ms_per_iteration": ms64 / sum(iters64)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "whole PCG iteration (own kernels + FP32 Poisson solve)",
+                     "traffic": None, "kernel": "whole mixed PCG iteration (own kernels + FP32 Poisson solve)",
                      "bytes_per_cell_iteration": PCG_BYTES_OWN + PCG_BYTES_POISSON,
                      "peak_source": f"{peak_kind} hbm_gbs"},
         "cpu_baseline": cpu, "e2e": None, "gpu_launches": None, "clocks": clocks,

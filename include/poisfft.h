@@ -198,23 +198,37 @@ int poisfft_batch_destroy(poisfft_batch* batch);
  * on every wall (staggered Dirichlet).  Operator: second-order fluxes with
  * harmonic-mean face coefficients 2 a_i a_j / (a_i + a_j); a wall face uses
  * the cell's a and the ghost value -phi.  For constant a it is a times the
- * Table 4 staggered-Dirichlet FD2 Laplacian.
+ * Table 4 staggered-Dirichlet FD2 Laplacian.  The paper gives no
+ * discretisation; this is the library's reading.
  * poisfft_pcg_create: a = cell coefficients (n0*n1*n2 floats, host or device,
  *   copied); a_ref > 0 is the preconditioner's constant coefficient, a_ref
  *   <= 0 selects the mean of a.  The preconditioner is an FP32
- *   poisfft_solve with staggered Dirichlet on every face.
+ *   poisfft_solve with staggered Dirichlet on every face.  At most 2^31 - 1
+ *   cells (POISFFT_ERR_UNSUPPORTED_SIZE).  Synchronises the device once.
  * poisfft_pcg_solve: phi (device doubles) holds the initial guess on entry
  *   and the solution on return; g (device doubles) the right-hand side.
- *   Flexible PCG in FP64 (vectors, operator, inner products) until
- *   ||g - A phi|| <= tol ||g|| or maxit iterations; *iters and *relres
- *   report what was reached.  Synchronises `stream` every iteration (the
- *   scalars of CG are read on the host).
- * poisfft_pcg_apply: out = -(A in) (device doubles), the operator alone.
- * No paper counterpart for the discretisation; it is this library's reading. */
+ *   Iterates until ||g - A phi|| <= tol ||g|| or maxit iterations; *iters
+ *   and *relres (either may be NULL) report the iterations and the relative
+ *   residual reached.  precision:
+ *     POISFFT_PCG_F64    flexible (Polak-Ribiere) PCG with FP64 vectors,
+ *                        operator and inner products;
+ *     POISFFT_PCG_MIXED  the same iteration in FP32 on a correction of phi,
+ *                        with reliable updates: phi and the true residual are
+ *                        refreshed in FP64 whenever the FP32 residual has
+ *                        dropped 1000-fold, and convergence is decided on the
+ *                        FP64 residual only (relres is that residual).
+ *   Blocks the calling thread: the convergence flag is read on the host one
+ *   iteration behind the device.  One solve at a time per object.
+ * poisfft_pcg_stats: out[0] iterations, out[1] FP64 (true) residual
+ *   evaluations, out[2] preconditioner solves, out[3] precision of the last
+ *   poisfft_pcg_solve.
+ * poisfft_pcg_apply: out = -(A in) (device doubles), the operator alone. */
+typedef enum { POISFFT_PCG_F64 = 0, POISFFT_PCG_MIXED = 1 } poisfft_pcg_precision;
 typedef struct poisfft_pcg poisfft_pcg;
 int poisfft_pcg_create(poisfft_pcg** out, const int64_t n[3], const double L[3], const float* a, double a_ref);
-int poisfft_pcg_solve(poisfft_pcg* pcg, double* phi, const double* g, double tol, int maxit, int* iters,
-                      double* relres, void* stream);
+int poisfft_pcg_solve(poisfft_pcg* pcg, double* phi, const double* g, double tol, int maxit, int precision,
+                      int* iters, double* relres, void* stream);
+int poisfft_pcg_stats(const poisfft_pcg* pcg, int64_t out[4]);
 int poisfft_pcg_apply(poisfft_pcg* pcg, double* out, const double* in, void* stream);
 int poisfft_pcg_destroy(poisfft_pcg* pcg);
 

@@ -18,6 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpoisfft.so")
 
 P, DR, DS, NR, NS = 0, 1, 2, 3, 4
+PCG_F64, PCG_MIXED = 0, 1
 SPECTRAL, FD2 = 0, 1
 F32, F64 = 0, 1
 
@@ -53,6 +54,7 @@ EXPORTED = [
     "poisfft_pcg_create",
     "poisfft_pcg_solve",
     "poisfft_pcg_apply",
+    "poisfft_pcg_stats",
     "poisfft_pcg_destroy",
 ]
 
@@ -117,8 +119,10 @@ def _load():
                                        ctypes.c_void_p, ctypes.c_double]
     lib.poisfft_pcg_create.restype = ctypes.c_int
     lib.poisfft_pcg_solve.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
-                                      ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
-                                      ctypes.c_void_p]
+                                      ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    lib.poisfft_pcg_stats.argtypes = [ctypes.c_void_p, i64p]
+    lib.poisfft_pcg_stats.restype = ctypes.c_int
     lib.poisfft_pcg_solve.restype = ctypes.c_int
     lib.poisfft_pcg_apply.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.poisfft_pcg_apply.restype = ctypes.c_int
@@ -372,15 +376,25 @@ class PCG:
             raise PoisFFTError(rc, "poisfft_pcg_create")
         self._h = h
 
-    def solve(self, phi, g, tol=1e-8, maxit=500, stream=None):
-        """phi: initial guess in, solution out (float64 device).  Returns (iterations, relres)."""
+    def solve(self, phi, g, tol=1e-8, maxit=500, stream=None, precision=None):
+        """phi: initial guess in, solution out (float64 device).  precision:
+        PCG_MIXED (default) or PCG_F64.  Returns (iterations, relres)."""
         it = ctypes.c_int()
         rel = ctypes.c_double()
-        rc = lib.poisfft_pcg_solve(self._h, _ptr(phi), _ptr(g), float(tol), int(maxit), ctypes.byref(it),
+        prec = PCG_MIXED if precision is None else int(precision)
+        rc = lib.poisfft_pcg_solve(self._h, _ptr(phi), _ptr(g), float(tol), int(maxit), prec, ctypes.byref(it),
                                    ctypes.byref(rel), _stream(stream))
         if rc != OK:
             raise PoisFFTError(rc, "poisfft_pcg_solve")
         return it.value, rel.value
+
+    def stats(self):
+        """Last solve: dict(iterations, true_residuals, preconditioner_solves, precision)."""
+        v = (ctypes.c_int64 * 4)()
+        rc = lib.poisfft_pcg_stats(self._h, v)
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_pcg_stats")
+        return dict(iterations=v[0], true_residuals=v[1], preconditioner_solves=v[2], precision=v[3])
 
     def apply(self, out, x, stream=None):
         """out = -(A x)."""

@@ -6,9 +6,11 @@
   operator, extracted by 27-colour probing) and against the oracle's PCG
   (same algorithm, FP64 preconditioner): iteration counts within 5 %,
   solutions within the accuracy the tolerance implies.
+* Both precisions: FP64 iteration and FP32 iteration with FP64 reliable
+  updates (the residual it reports is the FP64 one).
 * Special cases: constant a (the preconditioner is exact up to FP32
   rounding: a couple of iterations), g = 0, an initial guess that is already
-  the solution, the iteration cap.
+  the solution, the iteration cap, bitwise repeatability.
 """
 
 import numpy as np
@@ -56,68 +58,97 @@ def test_apply_matches_oracle(pb, n):
     assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
 
 
+PRECISIONS = ["f64", "mixed"]
+
+
+def _prec(pb, name):
+    return pb.PCG_F64 if name == "f64" else pb.PCG_MIXED
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("n,contrast,Ls", [
     ((24, 20, 16), 100.0, (1.0, 1.0, 1.0)),
     ((33, 17, 26), 10.0, (2.0, 1.0, 1.5)),
+    ((64, 32, 64), 100.0, (1.0, 0.5, 1.0)),     # specialised Poisson kernels as the preconditioner
 ])
-def test_solution_matches_exact_and_oracle_pcg(pb, n, contrast, Ls):
+def test_solution_matches_exact_and_oracle_pcg(pb, n, contrast, Ls, precision):
     a, g = _problem(n, contrast, 21)
     a64 = a.astype(np.float64)
-    A = _sparse_operator(a64, Ls)
-    exact = spla.splu(A).solve(g.ravel()).reshape(g.shape)
+    # exact discrete solution by sparse LU where that is quick (3D fill-in
+    # grows fast); the oracle's PCG and the true residual cover the rest
+    exact = None
+    if np.prod(n) <= 50000:
+        exact = spla.splu(_sparse_operator(a64, Ls)).solve(g.ravel()).reshape(g.shape)
     tol = 1e-11
-    ref, it_ref, rel_ref = V.pcg(g, a64, Ls, tol=tol, maxit=200)
+    ref, it_ref, rel_ref = V.pcg(g, a64, Ls, tol=tol, maxit=300)
     with pb.PCG(n, Ls, torch.from_numpy(a).cuda()) as s:
         gd = torch.from_numpy(g).cuda()
         phi = torch.zeros_like(gd)
-        it, rel = s.solve(phi, gd, tol=tol, maxit=200, stream=torch.cuda.current_stream())
+        it, rel = s.solve(phi, gd, tol=tol, maxit=300, stream=torch.cuda.current_stream(),
+                          precision=_prec(pb, precision))
         torch.cuda.synchronize()
+        stats = s.stats()
     phi = phi.cpu().numpy()
-    assert rel <= tol and it < 200
-    # the FP32 preconditioner perturbs the FP64 one by ~1e-7: a few more
-    # iterations at most at this tolerance
-    assert abs(it - it_ref) <= max(2, it_ref // 20), (it, it_ref)
+    assert rel <= tol and it < 300
+    if precision == "f64":
+        # the FP32 preconditioner perturbs the FP64 one by ~1e-7: a few more
+        # iterations at most at this tolerance
+        assert abs(it - it_ref) <= max(2, it_ref // 20), (it, it_ref)
+    else:
+        # FP32 iterations with FP64 residual replacement: close to the FP64 count
+        assert it <= it_ref + max(3, it_ref // 5), (it, it_ref)
+        assert stats["true_residuals"] >= 2
+    assert stats["iterations"] == it and stats["preconditioner_solves"] >= it
     true_rel = np.linalg.norm(g - V.apply_operator(phi, a64, Ls)) / np.linalg.norm(g)
-    assert true_rel <= 10 * tol
-    scale = np.max(np.abs(exact))
-    assert np.max(np.abs(phi - exact)) <= 1e-8 * scale
+    assert true_rel <= (1.01 if precision == "mixed" else 10) * tol
+    scale = np.max(np.abs(ref))
+    if exact is not None:
+        assert np.max(np.abs(phi - exact)) <= 1e-8 * scale
     assert np.max(np.abs(phi - ref)) <= 1e-8 * scale
 
 
-def test_constant_coefficient_converges_in_few_iterations(pb):
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_constant_coefficient_converges_in_few_iterations(pb, precision):
     n = (40, 30, 20)
     a = np.full(tuple(reversed(n)), 2.5, np.float32)
     g = W.normal(a.shape, 5)
     with pb.PCG(n, (1.0, 1.0, 1.0), torch.from_numpy(a).cuda()) as s:
         gd = torch.from_numpy(g).cuda()
         phi = torch.zeros_like(gd)
-        it, rel = s.solve(phi, gd, tol=1e-10, maxit=50)
+        it, rel = s.solve(phi, gd, tol=1e-10, maxit=50, precision=_prec(pb, precision))
     # the FP32 preconditioner is the exact inverse up to ~1e-7 relative
-    assert it <= 3 and rel <= 1e-10
+    assert it <= 4 and rel <= 1e-10
 
 
-def test_special_cases(pb):
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_special_cases(pb, precision):
     n = (16, 12, 10)
     a, g = _problem(n, 30.0, 8)
     Ls = (1.0, 1.0, 1.0)
+    prec = _prec(pb, precision)
     with pb.PCG(n, Ls, torch.from_numpy(a).cuda(), a_ref=1.0) as s:
         zero = torch.zeros(a.shape, dtype=torch.float64, device="cuda")
         phi = torch.zeros_like(zero)
-        assert s.solve(phi, zero, tol=1e-10) == (0, 0.0)
+        assert s.solve(phi, zero, tol=1e-10, precision=prec) == (0, 0.0)
         assert torch.count_nonzero(phi) == 0
         gd = torch.from_numpy(g).cuda()
-        it, rel = s.solve(phi, gd, tol=1e-12, maxit=300)
+        it, rel = s.solve(phi, gd, tol=1e-12, maxit=300, precision=prec)
         assert rel <= 1e-12
         again = phi.clone()
-        it2, rel2 = s.solve(again, gd, tol=1e-6, maxit=300)   # start at the solution
+        it2, rel2 = s.solve(again, gd, tol=1e-6, maxit=300, precision=prec)   # start at the solution
         assert it2 == 0 and rel2 <= 1e-6 and torch.equal(again, phi)
         capped = torch.zeros_like(gd)
-        it3, rel3 = s.solve(capped, gd, tol=1e-14, maxit=3)
+        it3, rel3 = s.solve(capped, gd, tol=1e-14, maxit=3, precision=prec)
         assert it3 == 3 and rel3 > 1e-14
-        # three iterations from zero are exactly the first three of the full run
+        # deterministic reductions: the same three iterations, bit for bit
         first3 = torch.zeros_like(gd)
-        s.solve(first3, gd, tol=0.0, maxit=3)
+        s.solve(first3, gd, tol=0.0, maxit=3, precision=prec)
         assert torch.equal(first3, capped)
+        if precision == "mixed":
+            # relres after the cap is the FP64 residual of the returned phi
+            p3 = capped.cpu().numpy()
+            true3 = np.linalg.norm(g - V.apply_operator(p3, a.astype(np.float64), Ls)) / np.linalg.norm(g)
+            assert abs(true3 - rel3) <= 1e-6 * true3
 
 
 def test_invalid_arguments(pb):
@@ -125,3 +156,9 @@ def test_invalid_arguments(pb):
         pb.PCG((0, 4, 4), (1.0, 1.0, 1.0), torch.ones(16, device="cuda"))
     with pytest.raises(pb.PoisFFTError):
         pb.PCG((4, 4, 4), (1.0, -1.0, 1.0), torch.ones(64, device="cuda"))
+    with pb.PCG((4, 4, 4), (1.0, 1.0, 1.0), torch.ones(64, device="cuda")) as s:
+        x = torch.zeros(64, dtype=torch.float64, device="cuda")
+        with pytest.raises(pb.PoisFFTError):
+            s.solve(x, x, precision=7)
+        with pytest.raises(pb.PoisFFTError):
+            s.solve(x, x, tol=-1.0)
