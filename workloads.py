@@ -129,19 +129,44 @@ BATCHES = {
 # Variable-coefficient problems div(a grad phi) = g (staggered Dirichlet on
 # every wall) solved by CG preconditioned with the FD2 Poisson solve.
 VC_PROBLEMS = {
-    # 256^3 cells on the unit cube, a log-normal with max/min = 100
+    # 256^3 cells on the unit cube, a = exp(c s), s a unit-variance Gaussian
+    # random field of correlation length 1/16, max(a)/min(a) = 100
     "pcg_vc_256_f64": dict(n=(256, 256, 256), Ls=(1.0, 1.0, 1.0), contrast=100.0, seed=5, tol=1e-8),
 }
 
 
-def lognormal_coefficient(shape, seed, contrast):
-    """Cell coefficients a = contrast ** (s / 2) with s a smooth Gaussian
-    random field (spectrum ~ |k|^-4) mapped affinely onto [-1, 1], so that
-    max(a) / min(a) = contrast and a spans [contrast^-1/2, contrast^1/2].
+def gaussian_random_field(shape, seed, corr_len, Ls=None):
+    """Unit-variance Gaussian random field with Gaussian covariance
+    exp(-r^2 / (2 corr_len^2)) on a periodic box of lengths Ls (default 1 per
+    axis): white N(0,1) noise filtered in Fourier space by the square root of
+    the covariance's spectrum, exp(-|k|^2 corr_len^2 / 4) with k = 2 pi m / L,
+    then scaled to unit sample variance (FP64)."""
+    import scipy.fft as sf
+
+    d = len(shape)
+    Ls = Ls or (1.0,) * d
+    f = rng(seed).standard_normal(size=shape)
+    spec = sf.rfftn(f, workers=-1)
+    k2 = 0.0
+    for ax, n in enumerate(shape):
+        L = Ls[d - 1 - ax]                              # numpy axis 0 is z (the last physical axis)
+        m = np.fft.rfftfreq(n, 1.0 / n) if ax == d - 1 else np.fft.fftfreq(n, 1.0 / n)
+        k = 2 * np.pi * m / L
+        k2 = k2 + (k ** 2).reshape([-1 if i == ax else 1 for i in range(d)])
+    spec *= np.exp(-k2 * corr_len ** 2 / 4.0)
+    field = sf.irfftn(spec, s=shape, workers=-1)
+    field -= field.mean()
+    return field / field.std()
+
+
+def lognormal_coefficient(shape, seed, contrast, corr_len=1.0 / 16):
+    """Cell coefficients a = exp(c s) with s a unit-variance Gaussian random
+    field of correlation length corr_len (gaussian_random_field) and c chosen
+    so that max(a) / min(a) = contrast (c = ln(contrast) / (max s - min s)).
     FP32 (the coefficient is stored in FP32 by the solver)."""
-    s = smooth_random_field(shape, seed, slope=-4.0, noise=0.0, dtype=np.float64)
-    s = 2.0 * (s - s.min()) / (s.max() - s.min()) - 1.0
-    return (float(contrast) ** (0.5 * s)).astype(np.float32)
+    s = gaussian_random_field(shape, seed, corr_len)
+    c = np.log(float(contrast)) / (s.max() - s.min())
+    return np.exp(c * s).astype(np.float32)
 
 
 def smooth_numbers(lo, hi, primes=(2, 3, 5, 7)):
