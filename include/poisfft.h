@@ -231,6 +231,68 @@ int poisfft_pcg_solve(poisfft_pcg* pcg, double* phi, const double* g, double tol
 int poisfft_pcg_stats(const poisfft_pcg* pcg, int64_t out[4]);
 int poisfft_pcg_apply(poisfft_pcg* pcg, double* out, const double* in, void* stream);
 int poisfft_pcg_destroy(poisfft_pcg* pcg);
+/* poisfft_pcg_set_coefficient: replace a (same grid; host or device floats)
+ *   and a_ref (<= 0: mean of a); recomputes the face coefficients.
+ *   Synchronises the device. */
+int poisfft_pcg_set_coefficient(poisfft_pcg* pcg, const float* a, double a_ref);
+
+/* ---- Learned initial guess for the PCG (no paper counterpart: the
+ * network is this library's addition on top of the Sec. 1 preconditioner) ----
+ * A spectral neural operator in the truncated sine basis of the walls:
+ *   v_0 = P f + p;  layer l < L: pre = W_l v_l + b_l + S_inv(R_l . S(v_l)),
+ *   v_{l+1} = gelu(pre) (identity for the last layer);  y = Q v_L + q,
+ * with S[m,j] = (2/n) sin(pi (m+1)(2j+1) / 2n) (K modes per axis),
+ * S_inv[j,m] = sin(pi (m+1)(2j+1) / 2n) and R_l one C x C matrix per mode.
+ * Features f of a right-hand side r (3 per cell): r / rms(r),
+ * (log a - mean) / std(log a), z / rms(z) with z = L_h^{-1} r (the FD2
+ * Poisson solve with staggered Dirichlet walls).  phi0 = z / a_ref solves the
+ * problem for the constant coefficient a_ref; the network's output y gives
+ * phi0 + rms(phi0) y.
+ * Parameters: one FP32 vector, in the order P (C x 3), p (C), per layer W
+ * (C x C), b (C), R (K^3 x C x C, mode (mz K + my) K + mx), then Q (C), q;
+ * the kernels use it rounded to bfloat16, with FP32 activations and sums.
+ * Arrays: activations and features [B][C or 3][n2][n1][n0], x fastest; y and
+ * targets [B][n2][n1][n0]; all device memory.
+ * poisfft_sno_num_params: parameter count, or -1 outside C <= 32, K <= 16,
+ *   L <= 8.
+ * poisfft_sno_create: grid n[3] (each >= modes), batch B; train = 1 keeps
+ *   the activations for poisfft_sno_backward and the optimiser state.
+ *   Parameters start at zero.
+ * poisfft_sno_set_params / _get_params: FP32 vector (host or device);
+ *   set_params also resets the optimiser state.  Synchronise the device.
+ * poisfft_sno_forward: y = network(feats) on `stream`.
+ * poisfft_sno_backward: grad = d(sum dy . y)/d(theta) for the activations
+ *   of the last forward (train objects only); grad is overwritten.
+ * poisfft_sno_loss: L = sum (y - t)^2 / sum t^2 over the batch (to *loss,
+ *   host, when non-NULL: synchronises `stream`) and dy = dL/dy (when dy is
+ *   non-NULL).
+ * poisfft_sno_adam: one Adam step (bias-corrected, step >= 1) on the FP32
+ *   parameters, then the bfloat16 copy is refreshed.
+ * poisfft_sno_info: out = {n0, n1, n2, B, C, K, L, train}.
+ * poisfft_pcg_features: the features of right-hand side g (device doubles)
+ *   for the PCG's coefficient into feats (3 N floats); when phi and target
+ *   are non-NULL also the training target (phi - phi0) / rms(phi0) (N floats).
+ * poisfft_pcg_learned_guess: phi (device doubles, overwritten) = phi0 +
+ *   rms(phi0) y for g, then `corrections` times: r = g - A phi (FP64),
+ *   phi += the same construction for r.  The network must have batch 1 and
+ *   the PCG's grid.  Synchronises nothing; pass phi to poisfft_pcg_solve. */
+typedef struct poisfft_sno poisfft_sno;
+int64_t poisfft_sno_num_params(int channels, int modes, int layers);
+int poisfft_sno_create(poisfft_sno** out, const int64_t n[3], int batch, int channels, int modes, int layers,
+                       int train);
+int poisfft_sno_set_params(poisfft_sno* sno, const float* theta);
+int poisfft_sno_get_params(const poisfft_sno* sno, float* theta);
+int poisfft_sno_forward(poisfft_sno* sno, float* y, const float* feats, void* stream);
+int poisfft_sno_backward(poisfft_sno* sno, float* grad, const float* dy, const float* feats, void* stream);
+int poisfft_sno_loss(poisfft_sno* sno, const float* y, const float* t, float* dy, double* loss, void* stream);
+int poisfft_sno_adam(poisfft_sno* sno, const float* grad, double lr, double beta1, double beta2, double eps, int step,
+                     void* stream);
+int poisfft_sno_info(const poisfft_sno* sno, int64_t out[8]);
+int poisfft_sno_destroy(poisfft_sno* sno);
+int poisfft_pcg_features(poisfft_pcg* pcg, const double* g, const double* phi, float* feats, float* target,
+                         void* stream);
+int poisfft_pcg_learned_guess(poisfft_pcg* pcg, poisfft_sno* sno, double* phi, const double* g, int corrections,
+                              void* stream);
 
 /* Per-launch timing for benchmarks (no paper counterpart; measurement aid).
  * When enabled, every solve records a CUDA event on its stream before each

@@ -56,6 +56,19 @@ EXPORTED = [
     "poisfft_pcg_apply",
     "poisfft_pcg_stats",
     "poisfft_pcg_destroy",
+    "poisfft_pcg_set_coefficient",
+    "poisfft_pcg_features",
+    "poisfft_pcg_learned_guess",
+    "poisfft_sno_num_params",
+    "poisfft_sno_create",
+    "poisfft_sno_set_params",
+    "poisfft_sno_get_params",
+    "poisfft_sno_forward",
+    "poisfft_sno_backward",
+    "poisfft_sno_loss",
+    "poisfft_sno_adam",
+    "poisfft_sno_info",
+    "poisfft_sno_destroy",
 ]
 
 
@@ -128,6 +141,26 @@ def _load():
     lib.poisfft_pcg_apply.restype = ctypes.c_int
     lib.poisfft_pcg_destroy.argtypes = [ctypes.c_void_p]
     lib.poisfft_pcg_destroy.restype = ctypes.c_int
+    vp, ci, cd = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.poisfft_pcg_set_coefficient.argtypes = [vp, vp, cd]
+    lib.poisfft_pcg_features.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.poisfft_pcg_learned_guess.argtypes = [vp, vp, vp, vp, ci, vp]
+    lib.poisfft_sno_num_params.argtypes = [ci, ci, ci]
+    lib.poisfft_sno_num_params.restype = ctypes.c_int64
+    lib.poisfft_sno_create.argtypes = [ctypes.POINTER(vp), i64p, ci, ci, ci, ci, ci]
+    lib.poisfft_sno_set_params.argtypes = [vp, vp]
+    lib.poisfft_sno_get_params.argtypes = [vp, vp]
+    lib.poisfft_sno_forward.argtypes = [vp, vp, vp, vp]
+    lib.poisfft_sno_backward.argtypes = [vp, vp, vp, vp, vp]
+    lib.poisfft_sno_loss.argtypes = [vp, vp, vp, vp, ctypes.POINTER(cd), vp]
+    lib.poisfft_sno_adam.argtypes = [vp, vp, cd, cd, cd, cd, ci, vp]
+    lib.poisfft_sno_info.argtypes = [vp, i64p]
+    lib.poisfft_sno_destroy.argtypes = [vp]
+    for name in ("poisfft_pcg_set_coefficient", "poisfft_pcg_features", "poisfft_pcg_learned_guess",
+                 "poisfft_sno_create", "poisfft_sno_set_params", "poisfft_sno_get_params", "poisfft_sno_forward",
+                 "poisfft_sno_backward", "poisfft_sno_loss", "poisfft_sno_adam", "poisfft_sno_info",
+                 "poisfft_sno_destroy"):
+        getattr(lib, name).restype = ci
     return lib
 
 
@@ -388,6 +421,25 @@ class PCG:
             raise PoisFFTError(rc, "poisfft_pcg_solve")
         return it.value, rel.value
 
+    def set_coefficient(self, a, a_ref=0.0):
+        """Replace the cell coefficients (same grid); a_ref <= 0: mean of a."""
+        rc = lib.poisfft_pcg_set_coefficient(self._h, _ptr(a), float(a_ref))
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_pcg_set_coefficient")
+
+    def features(self, g, feats, phi=None, target=None, stream=None):
+        """Network features of right-hand side g into feats (3 N float32);
+        with phi and target also the training target (N float32)."""
+        rc = lib.poisfft_pcg_features(self._h, _ptr(g), _ptr(phi), _ptr(feats), _ptr(target), _stream(stream))
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_pcg_features")
+
+    def learned_guess(self, sno, phi, g, corrections=1, stream=None):
+        """phi = the network's initial guess for g (plus `corrections` residual corrections)."""
+        rc = lib.poisfft_pcg_learned_guess(self._h, sno._h, _ptr(phi), _ptr(g), int(corrections), _stream(stream))
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_pcg_learned_guess")
+
     def stats(self):
         """Last solve: dict(iterations, true_residuals, preconditioner_solves, precision)."""
         v = (ctypes.c_int64 * 4)()
@@ -405,6 +457,73 @@ class PCG:
     def close(self):
         if self._h:
             lib.poisfft_pcg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def sno_num_params(channels, modes, layers):
+    return int(lib.poisfft_sno_num_params(int(channels), int(modes), int(layers)))
+
+
+class SNO:
+    """Spectral neural operator (truncated sine basis) for the learned PCG guess.
+
+    n: grid (x first); batch; channels C; modes K per axis; layers L; train:
+    keep activations for backward and the Adam state."""
+
+    def __init__(self, n, batch=1, channels=16, modes=12, layers=4, train=False):
+        h = ctypes.c_void_p()
+        n_arr = (ctypes.c_int64 * 3)(*[int(v) for v in n])
+        rc = lib.poisfft_sno_create(ctypes.byref(h), n_arr, int(batch), int(channels), int(modes), int(layers),
+                                    1 if train else 0)
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_sno_create")
+        self._h = h
+        self.n, self.batch, self.channels, self.modes, self.layers = tuple(n), batch, channels, modes, layers
+        self.num_params = sno_num_params(channels, modes, layers)
+
+    def _check(self, rc, what):
+        if rc != OK:
+            raise PoisFFTError(rc, what)
+
+    def set_params(self, theta):
+        self._check(lib.poisfft_sno_set_params(self._h, _ptr(theta)), "poisfft_sno_set_params")
+
+    def get_params(self, theta):
+        self._check(lib.poisfft_sno_get_params(self._h, _ptr(theta)), "poisfft_sno_get_params")
+
+    def forward(self, y, feats, stream=None):
+        self._check(lib.poisfft_sno_forward(self._h, _ptr(y), _ptr(feats), _stream(stream)), "poisfft_sno_forward")
+
+    def backward(self, grad, dy, feats, stream=None):
+        self._check(lib.poisfft_sno_backward(self._h, _ptr(grad), _ptr(dy), _ptr(feats), _stream(stream)),
+                    "poisfft_sno_backward")
+
+    def loss(self, y, t, dy=None, stream=None, read=True):
+        """Relative squared error (returned when read) and its gradient into dy."""
+        val = ctypes.c_double()
+        self._check(lib.poisfft_sno_loss(self._h, _ptr(y), _ptr(t), _ptr(dy), ctypes.byref(val) if read else None,
+                                         _stream(stream)), "poisfft_sno_loss")
+        return val.value if read else None
+
+    def adam(self, grad, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        self._check(lib.poisfft_sno_adam(self._h, _ptr(grad), float(lr), float(beta1), float(beta2), float(eps),
+                                         int(step), _stream(stream)), "poisfft_sno_adam")
+
+    def close(self):
+        if self._h:
+            lib.poisfft_sno_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -39,70 +39,17 @@
 #include <new>
 
 #include "../../include/poisfft.h"
+#include "reduce.cuh"
 
 namespace {
 
-constexpr int kBlock = 256;
+using pf::Reduce;
+using pf::grid_sum;
+constexpr int kBlock = pf::kReduceBlock;
 constexpr int kBlocksPerSM = 8;
 // FP32 residual reduction between two FP64 residual replacements; FP32
 // recursion keeps ~6 significant digits, so three decades are safe.
 constexpr double kReliableDelta = 1e-3;
-
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Deterministic grid-wide sums of K values per thread.  Each block writes its
-// K partial sums to part[k * gridDim.x + block]; the last block to finish
-// (counted with one atomic) adds the partials in a fixed order and stores the
-// totals to dst[k], then resets the counter.  The result does not depend on
-// the order in which blocks run, so repeated solves are bitwise identical.
-struct Reduce {
-  double* part;     // K * gridDim.x doubles
-  unsigned* count;  // zero between kernels
-};
-
-template <int K>
-__device__ __forceinline__ void grid_sum(const double (&v)[K], Reduce R, double* const (&dst)[K]) {
-  __shared__ double sh[K][kBlock / 32];
-  __shared__ bool last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < K; k++) {
-    const double w = warp_sum(v[k]);
-    if (lane == 0) sh[k][warp] = w;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < K; k++) {
-      double t = 0.0;
-      for (int w = 0; w < kBlock / 32; w++) t += sh[k][w];
-      R.part[(size_t)k * gridDim.x + blockIdx.x] = t;
-    }
-    __threadfence();
-    last = atomicAdd(R.count, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-#pragma unroll
-  for (int k = 0; k < K; k++) {
-    double t = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += kBlock) t += __ldcg(&R.part[(size_t)k * gridDim.x + b]);
-    t = warp_sum(t);
-    __syncthreads();
-    if (lane == 0) sh[k][warp] = t;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double u = 0.0;
-      for (int w = 0; w < kBlock / 32; w++) u += sh[k][w];
-      *dst[k] = u;
-    }
-  }
-  if (threadIdx.x == 0) *R.count = 0u;
-}
 
 struct Grid {
   int nx, ny, nz;
@@ -413,6 +360,87 @@ __global__ void __launch_bounds__(kBlock) mx_dir_kernel(float* __restrict__ p, c
   GRID_STRIDE(i, N) p[i] = first ? scale * zA[i] : scale * zA[i] + beta * p[i];
 }
 
+// ---- features of the learned initial guess --------------------------------
+
+// Sums that set the feature scales: r.r, z.z, sum log a, sum (log a)^2
+__global__ void __launch_bounds__(kBlock) feat_stats_kernel(const float* __restrict__ r, const float* __restrict__ z,
+                                                            const float* __restrict__ a, unsigned N, double* fs,
+                                                            Reduce R) {
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  GRID_STRIDE(i, N) {
+    const double ri = r[i], zi = z[i], la = logf(a[i]);
+    v[0] += ri * ri;
+    v[1] += zi * zi;
+    v[2] += la;
+    v[3] += la * la;
+  }
+  double* const d[4] = {&fs[0], &fs[1], &fs[2], &fs[3]};
+  grid_sum<4>(v, R, d);
+}
+
+struct FeatScale {
+  float inv_rms_r, inv_rms_z, mean_la, inv_sd_la;
+};
+
+__device__ __forceinline__ FeatScale feat_scale(const double* fs, unsigned N) {
+  FeatScale s;
+  const double rr = fs[0] / N, zz = fs[1] / N, mu = fs[2] / N;
+  const double var = fmax(fs[3] / N - mu * mu, 0.0);
+  s.inv_rms_r = rr > 0.0 ? (float)(1.0 / sqrt(rr)) : 0.f;
+  s.inv_rms_z = zz > 0.0 ? (float)(1.0 / sqrt(zz)) : 0.f;
+  s.mean_la = (float)mu;
+  s.inv_sd_la = var > 0.0 ? (float)(1.0 / sqrt(var)) : 1.f;
+  return s;
+}
+
+// feats = [r / rms(r), (log a - mean) / std, z / rms(z)]
+__global__ void __launch_bounds__(kBlock) feat_write_kernel(const float* __restrict__ r, const float* __restrict__ z,
+                                                            const float* __restrict__ a, const double* fs, unsigned N,
+                                                            float* __restrict__ feats) {
+  const FeatScale sc = feat_scale(fs, N);
+  GRID_STRIDE(i, N) {
+    feats[i] = r[i] * sc.inv_rms_r;
+    feats[(size_t)N + i] = (logf(a[i]) - sc.mean_la) * sc.inv_sd_la;
+    feats[2 * (size_t)N + i] = z[i] * sc.inv_rms_z;
+  }
+}
+
+// target = (phi - phi0) / rms(phi0), phi0 = z / a_ref
+__global__ void __launch_bounds__(kBlock) target_kernel(const double* __restrict__ phi, const float* __restrict__ z,
+                                                        double inv_aref, const double* fs, unsigned N,
+                                                        float* __restrict__ t) {
+  const double rz = sqrt(fs[1] / N);
+  const double s = rz > 0.0 ? 1.0 / (rz * inv_aref) : 0.0;
+  GRID_STRIDE(i, N) t[i] = (float)((phi[i] - (double)z[i] * inv_aref) * s);
+}
+
+// phi (=|+=) phi0 + rms(phi0) y
+__global__ void __launch_bounds__(kBlock) guess_kernel(double* __restrict__ phi, const float* __restrict__ z,
+                                                       const float* __restrict__ y, double inv_aref, const double* fs,
+                                                       unsigned N, int add) {
+  const double rp = sqrt(fs[1] / N) * inv_aref;
+  GRID_STRIDE(i, N) {
+    const double v = (double)z[i] * inv_aref + rp * (double)y[i];
+    phi[i] = add ? phi[i] + v : v;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) to_f32_kernel(const double* __restrict__ x, float* __restrict__ y,
+                                                        unsigned N) {
+  GRID_STRIDE(i, N) y[i] = (float)x[i];
+}
+
+// r = float(g - A phi) = float(g + K phi) with the FP64 operator
+__global__ void __launch_bounds__(kBlock) residual_kernel(const double* __restrict__ phi,
+                                                          const double* __restrict__ g, Faces<double> F,
+                                                          const float* __restrict__ a, Grid G, float* __restrict__ r) {
+  GRID_STRIDE(i, G.N) {
+    int x, y, z;
+    cell_xyz(G, i, x, y, z);
+    r[i] = (float)(g[i] + k_apply<double>(phi, F, a, G, i, x, y, z, phi[i]));
+  }
+}
+
 }  // namespace
 
 struct poisfft_pcg {
@@ -429,12 +457,15 @@ struct poisfft_pcg {
   // mixed iteration (r32 doubles as its residual)
   float *e = nullptr, *p32 = nullptr, *q32 = nullptr, *zb32 = nullptr;
   Scalars* S = nullptr;         // device
-  double* part = nullptr;       // 2 * nb partial sums
+  double* part = nullptr;       // 4 * nb partial sums
   unsigned* count = nullptr;    // last-block counter
   Scalars* hS = nullptr;        // pinned host copies, two slots
   cudaEvent_t ev[2] = {nullptr, nullptr};
   poisfft_plan* plan = nullptr;
   int64_t stats[4] = {0, 0, 0, 0};
+  // learned initial guess (allocated on first use)
+  float *feats = nullptr, *ybuf = nullptr;
+  double* fs = nullptr;         // feature sums
 };
 
 namespace {
@@ -442,7 +473,8 @@ namespace {
 void free_pcg(poisfft_pcg* s) {
   if (!s) return;
   void* bufs[] = {s->a, s->c64[0], s->c64[1], s->c64[2], s->c32[0], s->c32[1], s->c32[2], s->r, s->p, s->q,
-                  s->z, s->r32, s->z32, s->e, s->p32, s->q32, s->zb32, s->S, s->part, s->count};
+                  s->z, s->r32, s->z32, s->e, s->p32, s->q32, s->zb32, s->S, s->part, s->count,
+                  s->feats, s->ybuf, s->fs};
   for (void* b : bufs) cudaFree(b);
   if (s->hS) cudaFreeHost(s->hS);
   for (cudaEvent_t e : s->ev)
@@ -454,6 +486,48 @@ void free_pcg(poisfft_pcg* s) {
 template <typename T> Faces<T> faces_of(const poisfft_pcg* s);
 template <> Faces<double> faces_of<double>(const poisfft_pcg* s) { return Faces<double>{{s->c64[0], s->c64[1], s->c64[2]}}; }
 template <> Faces<float> faces_of<float>(const poisfft_pcg* s) { return Faces<float>{{s->c32[0], s->c32[1], s->c32[2]}}; }
+
+// Copy a, compute the face coefficients and a_ref (<= 0: the mean of a).
+int load_coefficient(poisfft_pcg* s, const float* a, double a_ref) {
+  const size_t N = s->N;
+  if (cudaMemcpy(s->a, a, N * sizeof(float), cudaMemcpyDefault) != cudaSuccess) return POISFFT_ERR_CUDA;
+  faces_kernel<<<s->nb, kBlock>>>(s->a, s->G, s->c64[0], s->c64[1], s->c64[2], s->c32[0], s->c32[1], s->c32[2]);
+  if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return POISFFT_ERR_CUDA;
+  if (a_ref > 0.0) {
+    s->a_ref = a_ref;
+    return POISFFT_OK;
+  }
+  float* h = new (std::nothrow) float[N];  // mean of a: host reduction once, FP64
+  if (!h) return POISFFT_ERR_ALLOC;
+  if (cudaMemcpy(h, s->a, N * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    delete[] h;
+    return POISFFT_ERR_CUDA;
+  }
+  double sum = 0.0;
+  for (size_t i = 0; i < N; i++) sum += h[i];
+  delete[] h;
+  s->a_ref = sum / (double)N;
+  return POISFFT_OK;
+}
+
+// Features of right-hand side g into s->feats; leaves z = L^{-1} g in s->z32
+// and the sums in s->fs.  `r_is_set`: s->r32 already holds the right-hand side.
+int learned_features(poisfft_pcg* s, const double* g, int r_is_set, cudaStream_t st) {
+  if (!s->feats) {
+    if (cudaMalloc(&s->feats, 3 * (size_t)s->N * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&s->ybuf, (size_t)s->N * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&s->fs, 4 * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return POISFFT_ERR_ALLOC;
+    }
+  }
+  if (!r_is_set) to_f32_kernel<<<s->nb, kBlock, 0, st>>>(g, s->r32, s->N);
+  int rc = poisfft_solve(s->plan, s->z32, s->r32, st);
+  if (rc != POISFFT_OK) return rc;
+  feat_stats_kernel<<<s->nb, kBlock, 0, st>>>(s->r32, s->z32, s->a, s->N, s->fs, Reduce{s->part, s->count});
+  feat_write_kernel<<<s->nb, kBlock, 0, st>>>(s->r32, s->z32, s->a, s->fs, s->N, s->feats);
+  return cudaGetLastError() == cudaSuccess ? POISFFT_OK : POISFFT_ERR_CUDA;
+}
 
 int publish(poisfft_pcg* s, int k, cudaStream_t st) {
   if (cudaMemcpyAsync(&s->hS[k & 1], s->S, sizeof(Scalars), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -612,7 +686,7 @@ int poisfft_pcg_create(poisfft_pcg** out, const int64_t n[3], const double L[3],
   float** d32[] = {&s->r32, &s->z32, &s->e, &s->p32, &s->q32, &s->zb32};
   for (float** b : d32) ok = ok && cudaMalloc(b, N * sizeof(float)) == cudaSuccess;
   ok = ok && cudaMalloc(&s->S, sizeof(Scalars)) == cudaSuccess &&
-       cudaMalloc(&s->part, 2 * sizeof(double) * s->nb) == cudaSuccess &&
+       cudaMalloc(&s->part, 4 * sizeof(double) * s->nb) == cudaSuccess &&
        cudaMalloc(&s->count, sizeof(unsigned)) == cudaSuccess &&
        cudaMallocHost(&s->hS, 2 * sizeof(Scalars)) == cudaSuccess &&
        cudaEventCreateWithFlags(&s->ev[0], cudaEventDisableTiming) == cudaSuccess &&
@@ -622,33 +696,13 @@ int poisfft_pcg_create(poisfft_pcg** out, const int64_t n[3], const double L[3],
     free_pcg(s);
     return POISFFT_ERR_ALLOC;
   }
-  if (cudaMemcpy(s->a, a, N * sizeof(float), cudaMemcpyDefault) != cudaSuccess ||
-      cudaMemset(s->count, 0, sizeof(unsigned)) != cudaSuccess) {
+  if (cudaMemset(s->count, 0, sizeof(unsigned)) != cudaSuccess) {
     free_pcg(s);
     return POISFFT_ERR_CUDA;
   }
-  faces_kernel<<<s->nb, kBlock>>>(s->a, s->G, s->c64[0], s->c64[1], s->c64[2], s->c32[0], s->c32[1], s->c32[2]);
-  if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+  if ((rc = load_coefficient(s, a, a_ref)) != POISFFT_OK) {
     free_pcg(s);
-    return POISFFT_ERR_CUDA;
-  }
-  if (a_ref > 0.0) {
-    s->a_ref = a_ref;
-  } else {  // mean of a (host reduction once, FP64)
-    float* h = new (std::nothrow) float[N];
-    if (!h) {
-      free_pcg(s);
-      return POISFFT_ERR_ALLOC;
-    }
-    if (cudaMemcpy(h, s->a, N * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) {
-      delete[] h;
-      free_pcg(s);
-      return POISFFT_ERR_CUDA;
-    }
-    double sum = 0.0;
-    for (size_t i = 0; i < N; i++) sum += h[i];
-    delete[] h;
-    s->a_ref = sum / (double)N;
+    return rc;
   }
   *out = s;
   return POISFFT_OK;
@@ -674,6 +728,41 @@ int poisfft_pcg_stats(const poisfft_pcg* s, int64_t out[4]) {
   if (!s || !out) return POISFFT_ERR_INVALID_ARG;
   for (int i = 0; i < 4; i++) out[i] = s->stats[i];
   return POISFFT_OK;
+}
+
+int poisfft_pcg_set_coefficient(poisfft_pcg* s, const float* a, double a_ref) {
+  if (!s || !a) return POISFFT_ERR_INVALID_ARG;
+  return load_coefficient(s, a, a_ref);
+}
+
+int poisfft_pcg_features(poisfft_pcg* s, const double* g, const double* phi, float* feats, float* target,
+                         void* stream) {
+  if (!s || !g || !feats) return POISFFT_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int rc = learned_features(s, g, 0, st);
+  if (rc != POISFFT_OK) return rc;
+  if (cudaMemcpyAsync(feats, s->feats, 3 * (size_t)s->N * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return POISFFT_ERR_CUDA;
+  if (phi && target) target_kernel<<<s->nb, kBlock, 0, st>>>(phi, s->z32, 1.0 / s->a_ref, s->fs, s->N, target);
+  return cudaGetLastError() == cudaSuccess ? POISFFT_OK : POISFFT_ERR_CUDA;
+}
+
+int poisfft_pcg_learned_guess(poisfft_pcg* s, poisfft_sno* sno, double* phi, const double* g, int corrections,
+                              void* stream) {
+  if (!s || !sno || !phi || !g || corrections < 0) return POISFFT_ERR_INVALID_ARG;
+  int64_t info[8];
+  if (poisfft_sno_info(sno, info) != POISFFT_OK) return POISFFT_ERR_INVALID_ARG;
+  if (info[0] != s->G.nx || info[1] != s->G.ny || info[2] != s->G.nz || info[3] != 1) return POISFFT_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const double inv_aref = 1.0 / s->a_ref;
+  for (int c = 0; c <= corrections; c++) {
+    if (c > 0) residual_kernel<<<s->nb, kBlock, 0, st>>>(phi, g, faces_of<double>(s), s->a, s->G, s->r32);
+    int rc = learned_features(s, g, c > 0, st);
+    if (rc != POISFFT_OK) return rc;
+    if ((rc = poisfft_sno_forward(sno, s->ybuf, s->feats, stream)) != POISFFT_OK) return rc;
+    guess_kernel<<<s->nb, kBlock, 0, st>>>(phi, s->z32, s->ybuf, inv_aref, s->fs, s->N, c > 0);
+  }
+  return cudaGetLastError() == cudaSuccess ? POISFFT_OK : POISFFT_ERR_CUDA;
 }
 
 int poisfft_pcg_destroy(poisfft_pcg* s) {
