@@ -74,7 +74,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
-                    choices=sorted(W.WORKLOADS) + sorted(W.BATCHES) + sorted(W.VC_PROBLEMS))
+                    choices=sorted(W.WORKLOADS) + sorted(W.BATCHES) + sorted(W.VC_PROBLEMS) + sorted(W.LEARNED))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 error check of the solution")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -566,6 +566,95 @@ def run_pcg(args):
     return 0
 
 
+def run_learned(args):
+    """Learned form: train the spectral neural operator on pairs from the
+    library's PCG (coarse grid), then time the PCG on the 256^3 problem from
+    phi = 0 and from the learned guess (0, 1, 2 residual corrections), to the
+    same relative residual.  One step = one solve including the network."""
+    import torch
+
+    from paper_1409_8116_gb300 import binding as pb
+    from paper_1409_8116_gb300 import learned
+
+    spec = W.LEARNED[args.workload]
+    ev = W.VC_PROBLEMS[spec["eval"]]
+    arch = spec["arch"]
+    t0 = time.perf_counter()
+    samples = W.learned_samples(spec["n_train"], spec["pairs"] + spec["holdout"], spec["seed"], spec["contrast"])
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    feats, targets, info = learned.generate_pairs(spec["n_train"], ev["Ls"], samples, tol=spec["pair_tol"])
+    t_pairs = time.perf_counter() - t0
+    theta, hist = learned.train((feats, targets), spec["n_train"], batch=spec["batch"], epochs=spec["epochs"],
+                                lr=spec["lr"], seed=spec["seed"], holdout=spec["holdout"], **arch)
+    del feats, targets
+    torch.cuda.empty_cache()
+
+    def solve_set(n, Ls, a, g, net, steps, warm):
+        out = {}
+        stream = torch.cuda.Stream()
+        with pb.PCG(n, Ls, torch.from_numpy(a).cuda()) as pcg:
+            gd = torch.from_numpy(g).cuda()
+            phi = torch.zeros_like(gd)
+            for mode in ("plain", "learned0", "learned1", "learned2"):
+                corr = None if mode == "plain" else int(mode[-1])
+
+                def one():
+                    if corr is None:
+                        phi.zero_()
+                    else:
+                        pcg.learned_guess(net, phi, gd, corrections=corr, stream=stream)
+                    return pcg.solve(phi, gd, tol=ev["tol"], maxit=1000, stream=stream)
+
+                with torch.cuda.stream(stream):
+                    for _ in range(warm):
+                        one()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for _ in range(steps):
+                        it, rel = one()
+                    e1.record(stream)
+                stream.synchronize()
+                out[mode] = {"ms": e0.elapsed_time(e1) / steps, "iterations": it, "relres": rel}
+        return out
+
+    shape = tuple(reversed(ev["n"]))
+    a = W.lognormal_coefficient(shape, ev["seed"], ev["contrast"])
+    g = W.normal(shape, ev["seed"] + 1)
+    net = learned.load_network(ev["n"], theta, **arch)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    res = solve_set(ev["n"], ev["Ls"], a, g, net, args.steps, args.warmup)
+    clocks = sampler.stop()
+    net.close()
+    net64 = learned.load_network(spec["n_train"], theta, **arch)
+    held = []
+    for a_h, g_h in samples[spec["pairs"]:spec["pairs"] + 4]:
+        r = solve_set(spec["n_train"], ev["Ls"], a_h, g_h, net64, 2, 1)
+        held.append({k: v["iterations"] for k, v in r.items()})
+    net64.close()
+    best = min(("learned0", "learned1", "learned2"), key=lambda k: res[k]["ms"])
+    line = {
+        "metric": "learned PCG: time to 1e-8 relative residual, plain FFT-preconditioned PCG / with the learned guess",
+        "value": res["plain"]["ms"] / res[best]["ms"], "unit": "x (speedup, >1 = learned faster)",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res[best]["ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "network bf16 weights / f32 activations; PCG f32 iterations + f64 reliable updates",
+        "data": "synthetic", "config": {"workload": args.workload, "eval": spec["eval"], "n": list(ev["n"]),
+                                        "n_train": list(spec["n_train"]), "pairs": spec["pairs"], **arch,
+                                        "epochs": spec["epochs"], "batch": spec["batch"]},
+        "eval_256": res, "best": best, "heldout_train_grid_iterations": held,
+        "train": {"host_gen_s": t_gen, "pairs_s": t_pairs, "train_s": hist["seconds"],
+                  "loss_first_epoch": hist["train_loss"][0], "loss_last_epoch": hist["train_loss"][-1],
+                  "holdout_loss": hist["holdout_loss"][-1] if hist["holdout_loss"] else None,
+                  "pair_pcg_iterations_mean": float(np.mean(info["pcg_iterations"]))},
+        "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -574,6 +663,8 @@ def main():
         return run_batch(args)
     if args.workload in W.VC_PROBLEMS:
         return run_pcg(args)
+    if args.workload in W.LEARNED:
+        return run_learned(args)
     return run_ours(args)
 
 

@@ -219,6 +219,141 @@ __global__ void __launch_bounds__(kT) point_kernel(const float* __restrict__ v, 
   }
 }
 
+// Specialised forms of row_contract_kernel and point_kernel for compile-time
+// K and C (the inference configuration): the matrix sits in shared memory,
+// the row loads are issued four at a time, and every loop over channels and
+// modes is unrolled (vectorised loads of the expansion rows).
+template <int K>
+__global__ void __launch_bounds__(kT) row_contract_k_kernel(const float* __restrict__ in, const float* __restrict__ M,
+                                                            float* __restrict__ out, long long rows, int n) {
+  // Two rows per warp pass, so that the loads and the shuffle reductions of
+  // one row overlap those of the other.
+  extern __shared__ float sM[];  // K x n
+  for (int i = threadIdx.x; i < K * n; i += blockDim.x) sM[i] = M[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long r = 2 * warp; r < rows; r += 2 * nwarps) {
+    const bool two = r + 1 < rows;
+    float a0[K], a1[K];
+#pragma unroll
+    for (int m = 0; m < K; m++) a0[m] = a1[m] = 0.f;
+    const float* s0 = in + r * n;
+    const float* s1 = in + (two ? r + 1 : r) * n;
+    for (int j0 = lane; j0 < n; j0 += 64) {
+      const int j1 = j0 + 32;
+      const float x0 = s0[j0], y0 = s1[j0];
+      const float x1 = j1 < n ? s0[j1] : 0.f, y1 = j1 < n ? s1[j1] : 0.f;
+#pragma unroll
+      for (int m = 0; m < K; m++) {
+        const float c0 = sM[m * n + j0];
+        a0[m] += c0 * x0;
+        a1[m] += c0 * y0;
+      }
+      if (j1 < n) {
+#pragma unroll
+        for (int m = 0; m < K; m++) {
+          const float c1 = sM[m * n + j1];
+          a0[m] += c1 * x1;
+          a1[m] += c1 * y1;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int m = 0; m < K; m++) {
+        a0[m] += __shfl_down_sync(0xffffffffu, a0[m], o);
+        a1[m] += __shfl_down_sync(0xffffffffu, a1[m], o);
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int m = 0; m < K; m++) {
+        out[r * K + m] = a0[m];
+        if (two) out[(r + 1) * K + m] = a1[m];
+      }
+    }
+  }
+}
+
+template <int C, int K>
+__global__ void __launch_bounds__(kT) point_ck_kernel(const float* __restrict__ v, const float* __restrict__ U,
+                                                      const float* __restrict__ E,
+                                                      const __nv_bfloat16* __restrict__ th, long long oW,
+                                                      long long ob, float* __restrict__ pre_out,
+                                                      float* __restrict__ out, int act, Dims D) {
+  // Blocks take whole x rows (R rows at a time when nx < 256) so that the
+  // expansion rows U[b][o][z,y][0..K) of those rows are staged in shared
+  // memory once: no global load remains inside the loop over outputs.
+  static_assert(K % 4 == 0 && C % 4 == 0, "vectorised rows");
+  constexpr int RMAX = 8;
+  __shared__ __align__(16) float sW[C * C];
+  __shared__ float sb[C];
+  __shared__ __align__(16) float sU[RMAX][C * K];
+  for (int i = threadIdx.x; i < C * C; i += blockDim.x) sW[i] = wload(th, oW + i);
+  for (int i = threadIdx.x; i < C; i += blockDim.x) sb[i] = wload(th, ob + i);
+  const int R = D.nx >= kT ? 1 : min(RMAX, kT / D.nx);
+  const long long rows = (long long)D.nz * D.ny;   // rows per sample
+  const long long all_rows = (long long)D.B * rows;
+  const int lr = threadIdx.x / D.nx < R ? threadIdx.x / D.nx : R;  // this thread's row in the group
+  const int x0 = D.nx >= kT ? threadIdx.x : threadIdx.x - lr * D.nx;
+  const int xstep = D.nx >= kT ? kT : D.nx;
+  for (long long r0 = (long long)blockIdx.x * R; r0 < all_rows; r0 += (long long)gridDim.x * R) {
+    __syncthreads();  // previous group's rows are no longer read
+    for (int e = threadIdx.x; e < R * C * K; e += blockDim.x) {
+      const int g = e / (C * K), o = (e / K) % C, m = e % K;
+      const long long row = r0 + g;
+      float val = 0.f;
+      if (row < all_rows) {
+        const long long b = row / rows, zy = row - b * rows;
+        val = U[((b * C + o) * rows + zy) * K + m];
+      }
+      sU[g][o * K + m] = val;
+    }
+    __syncthreads();
+    const long long row = r0 + lr;
+    if (lr >= R || row >= all_rows) continue;
+    const long long b = row / rows, zy = row - b * rows;
+    for (int x = x0; x < D.nx; x += xstep) {
+      const long long p = zy * D.nx + x;
+      float vin[C];
+#pragma unroll
+      for (int i = 0; i < C; i++) vin[i] = v[(b * C + i) * D.N + p];
+      float e[K];
+      const float4* e4 = reinterpret_cast<const float4*>(E + (long long)x * K);
+#pragma unroll
+      for (int q = 0; q < K / 4; q++) {
+        const float4 t = __ldg(e4 + q);
+        e[4 * q] = t.x;
+        e[4 * q + 1] = t.y;
+        e[4 * q + 2] = t.z;
+        e[4 * q + 3] = t.w;
+      }
+#pragma unroll
+      for (int o = 0; o < C; o++) {
+        float acc = sb[o];
+        const float4* w4 = reinterpret_cast<const float4*>(sW + o * C);
+#pragma unroll
+        for (int q = 0; q < C / 4; q++) {
+          const float4 w = w4[q];
+          acc += w.x * vin[4 * q] + w.y * vin[4 * q + 1] + w.z * vin[4 * q + 2] + w.w * vin[4 * q + 3];
+        }
+        const float4* u4 = reinterpret_cast<const float4*>(&sU[lr][o * K]);
+#pragma unroll
+        for (int q = 0; q < K / 4; q++) {
+          const float4 u = u4[q];
+          acc += e[4 * q] * u.x + e[4 * q + 1] * u.y + e[4 * q + 2] * u.z + e[4 * q + 3] * u.w;
+        }
+        const long long at = (b * C + o) * D.N + p;
+        if (pre_out) pre_out[at] = acc;
+        out[at] = act ? gelu(acc) : acc;
+      }
+    }
+  }
+}
+
 // y[b,p] = sum_c Q[c] v[b,c,p] + q
 __global__ void __launch_bounds__(kT) proj_kernel(const float* __restrict__ v, const __nv_bfloat16* __restrict__ th,
                                                   long long oQ, long long oq, float* __restrict__ y, Dims D) {
@@ -446,12 +581,23 @@ unsigned grid_for(long long n, int sms) {
   return (unsigned)std::max<long long>(1, std::min<long long>((n + kT - 1) / kT, (long long)sms * 16));
 }
 
+// out[row][m] = sum_j M[m][j] in[row][j]; the K = 12 form stages M in smem.
+void row_contract(poisfft_sno* s, const float* in, const float* M, float* out, long long rows, int n, int K,
+                  cudaStream_t st) {
+  const size_t smem = (size_t)K * n * sizeof(float);
+  if (K == 12 && smem <= 48 * 1024) {
+    row_contract_k_kernel<12><<<grid_for(rows * 32, s->sms), kT, smem, st>>>(in, M, out, rows, n);
+  } else {
+    row_contract_kernel<<<grid_for(rows * 32, s->sms), kT, 0, st>>>(in, M, out, rows, n, K);
+  }
+}
+
 // Truncated sine analysis / synthesis along the three axes (forward pass).
 void analysis(poisfft_sno* s, const float* v, float* vh, cudaStream_t st) {
   const Dims& D = s->D;
   const long long BC = (long long)D.B * D.C;
   const long long rows = BC * D.nz * D.ny;
-  row_contract_kernel<<<grid_for(rows * 32, s->sms), kT, 0, st>>>(v, s->Sa[0], s->T1, rows, D.nx, D.K);
+  row_contract(s, v, s->Sa[0], s->T1, rows, D.nx, D.K, st);
   axis_contract_kernel<<<grid_for(BC * D.nz * D.K * D.K, s->sms), kT, 0, st>>>(s->T1, s->Sa[1], s->T2, BC * D.nz,
                                                                               D.ny, D.K, D.K);
   axis_contract_kernel<<<grid_for(BC * D.K * D.K * D.K, s->sms), kT, 0, st>>>(s->T2, s->Sa[2], vh, BC, D.nz, D.K,
@@ -622,8 +768,13 @@ int poisfft_sno_forward(poisfft_sno* s, float* y, const float* feats, void* stre
     mix_kernel<<<grid_for((long long)D.B * D.C * D.K * D.K * D.K, s->sms), kT, 0, st>>>(
         vh, s->thb, O.R[l], s->uh, D.B, D.C, D.K * D.K * D.K);
     synthesis_zy(s, s->Si, s->uh, s->T1, st);
-    point_kernel<<<gp, kT, 0, st>>>(cur, s->T1, s->Si[0], s->thb, O.W[l], O.b[l], s->train ? s->pre[l] : nullptr,
-                                    nxt, l < D.L - 1 ? 1 : 0, D);
+    float* pre = s->train ? s->pre[l] : nullptr;
+    const int act = l < D.L - 1 ? 1 : 0;
+    if (D.C == 16 && D.K == 12 && D.nx >= 32)
+      point_ck_kernel<16, 12><<<grid_for((long long)D.B * D.nz * D.ny * 32, s->sms), kT, 0, st>>>(
+          cur, s->T1, s->Si[0], s->thb, O.W[l], O.b[l], pre, nxt, act, D);
+    else
+      point_kernel<<<gp, kT, 0, st>>>(cur, s->T1, s->Si[0], s->thb, O.W[l], O.b[l], pre, nxt, act, D);
     cur = nxt;
   }
   proj_kernel<<<gp, kT, 0, st>>>(cur, s->thb, O.Q, O.q, y, D);
@@ -652,7 +803,7 @@ int poisfft_sno_backward(poisfft_sno* s, float* grad, const float* dy, const flo
     weight_grad(s, s->dpre, D.C, nullptr, 1, grad + O.b[l], st);
     // spectral path: duh = S_inv^T(dpre)
     const long long rows = BC * D.nz * D.ny;
-    row_contract_kernel<<<grid_for(rows * 32, s->sms), kT, 0, st>>>(s->dpre, s->SiT[0], s->T1, rows, D.nx, D.K);
+    row_contract(s, s->dpre, s->SiT[0], s->T1, rows, D.nx, D.K, st);
     axis_contract_kernel<<<grid_for(BC * D.nz * D.K * D.K, s->sms), kT, 0, st>>>(s->T1, s->SiT[1], s->T2,
                                                                                 BC * D.nz, D.ny, D.K, D.K);
     axis_contract_kernel<<<grid_for(BC * M3, s->sms), kT, 0, st>>>(s->T2, s->SiT[2], s->uh, BC, D.nz, D.K,

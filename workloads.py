@@ -135,6 +135,29 @@ VC_PROBLEMS = {
 }
 
 
+# Learned form: training pairs on a coarser grid from the same coefficient
+# recipe (contrast drawn log-uniformly in [10, 100] per pair), evaluated on
+# the 256^3 problem above and on held-out pairs of the training grid.
+LEARNED = {
+    "learned_pcg_256": dict(eval="pcg_vc_256_f64", n_train=(64, 64, 64), pairs=2000, holdout=16, seed=11,
+                            contrast=(10.0, 100.0), arch=dict(channels=16, modes=12, layers=4),
+                            batch=8, epochs=20, lr=2e-3, pair_tol=1e-6),
+}
+
+
+def learned_samples(n, count, seed, contrast=(10.0, 100.0)):
+    """(a, g) host pairs for training: a = lognormal_coefficient with a
+    contrast drawn log-uniformly from `contrast`, g standard normal; pair k
+    uses coefficient seed 1000 + k and right-hand-side seed 5000 + k."""
+    shape = tuple(reversed(n))
+    r = rng(seed)
+    out = []
+    for k in range(count):
+        c = float(np.exp(r.uniform(np.log(contrast[0]), np.log(contrast[1]))))
+        out.append((lognormal_coefficient(shape, 1000 + k, c), normal(shape, 5000 + k)))
+    return out
+
+
 def gaussian_random_field(shape, seed, corr_len, Ls=None):
     """Unit-variance Gaussian random field with Gaussian covariance
     exp(-r^2 / (2 corr_len^2)) on a periodic box of lengths Ls (default 1 per
