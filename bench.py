@@ -236,6 +236,11 @@ def run_reference(args):
     return 0
 
 
+def plan_singular(bcs):
+    """Every axis periodic or Neumann: the solve removes the zero mode."""
+    return all(b in (0, 3, 4) for b in bcs)
+
+
 def workload_config(name, spec):
     nx, ny, nz = spec["n"]
     return {"workload": name, "n": [nx, ny, nz], "bcs": [BC_NAME[b] for b in spec["bcs"]],
@@ -346,6 +351,13 @@ def run_ours(args):
         err = O.rel_max_error(phi.cpu().numpy().astype(np.float64), ref)
         del ref
         print(f"# FP64 check {time.perf_counter() - t_chk:.1f} s", file=sys.stderr)
+    zero_mode = None
+    if rank == 0 and plan_singular(spec["bcs"]):
+        zero_mode = {"mean_fp64_gpu": plan.zero_mode_mean(g, stream)}
+        if not args.no_check:
+            from oracle import poisson as O
+
+            zero_mode["mean_fp64_oracle"] = O.weighted_mean(g_host.astype(np.float64), spec["bcs"])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -357,7 +369,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if f64 else "f32", "data": "synthetic",
             "config": workload_config(args.workload, spec),
-            "max_rel_err_vs_fp64": err,
+            "max_rel_err_vs_fp64": err, "zero_mode": zero_mode,
             "hbm_frac_step": step_bytes * args.steps / (ms_max / 1e3) / 1e9 / peak,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -622,6 +634,25 @@ def run_learned(args):
     a = W.lognormal_coefficient(shape, ev["seed"], ev["contrast"])
     g = W.normal(shape, ev["seed"] + 1)
     net = learned.load_network(ev["n"], theta, **arch)
+    # network inference alone (one forward on the 256^3 features)
+    Nc = int(np.prod(ev["n"]))
+    fin = torch.randn((3, Nc), device="cuda")
+    yout = torch.empty(Nc, device="cuda")
+    for _ in range(2):
+        net.forward(yout, fin)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        net.forward(yout, fin)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / 5
+    C, Lyr = arch["channels"], arch["layers"]
+    # algorithmic bytes per cell of one forward (FP32 activations): lifting
+    # reads 3 features and writes C channels; per layer the sine analysis reads
+    # C, the channel mixing reads C and writes C; the projection reads C, writes 1
+    fwd_bytes = Nc * 4 * ((3 + C) + Lyr * 3 * C + (C + 1))
+    del fin, yout
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)
@@ -649,7 +680,12 @@ def run_learned(args):
                   "loss_first_epoch": hist["train_loss"][0], "loss_last_epoch": hist["train_loss"][-1],
                   "holdout_loss": hist["holdout_loss"][-1] if hist["holdout_loss"] else None,
                   "pair_pcg_iterations_mean": float(np.mean(info["pcg_iterations"]))},
-        "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clocks,
+        "network_forward_ms": fwd_ms,
+        "roofline": {"bound": "hbm", "achieved": fwd_bytes / (fwd_ms / 1e3) / 1e9, "peak": load_peaks()[0],
+                     "unit": "GB/s", "frac": fwd_bytes / (fwd_ms / 1e3) / 1e9 / load_peaks()[0], "traffic": None,
+                     "kernel": "network forward at 256^3 (all its kernels)",
+                     "bytes_per_cell": fwd_bytes / Nc, "peak_source": f"{load_peaks()[1]} hbm_gbs"},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -294,6 +294,16 @@ int poisfft_pcg_features(poisfft_pcg* pcg, const double* g, const double* phi, f
 int poisfft_pcg_learned_guess(poisfft_pcg* pcg, poisfft_sno* sno, double* phi, const double* g, int corrections,
                               void* stream);
 
+/* Zero mode of a singular problem (every axis P, NR or NS), which the solve
+ * removes from g (the paper does not discuss it; the reading: the all-zero
+ * spectral coefficient is set to 0).  *mean = sum w g / sum w with w = 1/2
+ * at both ends of NR axes (the k = 0 row of the Table 2 forward
+ * transforms) and 1 elsewhere, summed with compensation per thread and in
+ * FP64 across threads.  g: device array of the plan's dtype, dense.
+ * POISFFT_ERR_INVALID_ARG for a plan that is not singular.  Synchronises
+ * `stream`. */
+int poisfft_zero_mode_mean(poisfft_plan* plan, const void* g, double* mean, void* stream);
+
 /* Per-launch timing for benchmarks (no paper counterpart; measurement aid).
  * When enabled, every solve records a CUDA event on its stream before each
  * kernel launch and after the last one.  Host cost: one event record per

@@ -69,6 +69,7 @@ EXPORTED = [
     "poisfft_sno_adam",
     "poisfft_sno_info",
     "poisfft_sno_destroy",
+    "poisfft_zero_mode_mean",
 ]
 
 
@@ -156,6 +157,8 @@ def _load():
     lib.poisfft_sno_adam.argtypes = [vp, vp, cd, cd, cd, cd, ci, vp]
     lib.poisfft_sno_info.argtypes = [vp, i64p]
     lib.poisfft_sno_destroy.argtypes = [vp]
+    lib.poisfft_zero_mode_mean.argtypes = [vp, vp, ctypes.POINTER(cd), vp]
+    lib.poisfft_zero_mode_mean.restype = ci
     for name in ("poisfft_pcg_set_coefficient", "poisfft_pcg_features", "poisfft_pcg_learned_guess",
                  "poisfft_sno_create", "poisfft_sno_set_params", "poisfft_sno_get_params", "poisfft_sno_forward",
                  "poisfft_sno_backward", "poisfft_sno_loss", "poisfft_sno_adam", "poisfft_sno_info",
@@ -283,6 +286,14 @@ class Plan:
         if rc != OK:
             raise PoisFFTError(rc, "poisfft_plan_info")
         return dict(launches=info[0], workspace_bytes=info[1], dominant_bytes=info[2], dominant_index=info[3])
+
+    def zero_mode_mean(self, g, stream=None):
+        """Weighted mean of g that the solve of a singular problem removes (FP64)."""
+        m = ctypes.c_double()
+        rc = lib.poisfft_zero_mode_mean(self._p, _ptr(g), ctypes.byref(m), _stream(stream))
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_zero_mode_mean")
+        return m.value
 
     def launches(self):
         """Per launch position: dict(bytes, kernel, mode, axis)."""

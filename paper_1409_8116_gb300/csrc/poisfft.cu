@@ -23,6 +23,7 @@
 
 #include "../../include/poisfft.h"
 #include "fast_kernels.cuh"
+#include "reduce.cuh"
 #include "internal.h"
 #include "launch.h"
 
@@ -361,6 +362,8 @@ struct poisfft_plan {
   void* lam[3] = {nullptr, nullptr, nullptr};
   int* perm[3] = {nullptr, nullptr, nullptr};
   int* err = nullptr;
+  double* zm = nullptr;               // zero-mode reduction: 1 result + 2 * blocks partials
+  unsigned* zm_count = nullptr;
   std::vector<CUtensorMap> maps;      // one per launch (strided launches use theirs)
   std::vector<SweepLaunch> sweeps;
   void* stage_g = nullptr;
@@ -386,6 +389,8 @@ void free_plan(poisfft_plan* p) {
     if (p->perm[i]) cudaFree(p->perm[i]);
   }
   if (p->err) cudaFree(p->err);
+  if (p->zm) cudaFree(p->zm);
+  if (p->zm_count) cudaFree(p->zm_count);
   if (p->stage_g) cudaFree(p->stage_g);
   if (p->stage_phi) cudaFree(p->stage_phi);
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
@@ -1053,6 +1058,79 @@ int poisfft_plan_info(const poisfft_plan* p, int64_t info[4]) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Zero mode of singular problems, reported in FP64
+// ---------------------------------------------------------------------------
+// The solve sets the all-zero spectral coefficient to 0, i.e. removes the
+// weighted mean of g (weights 1/2 at both ends of NR axes, 1 elsewhere).
+// Per-thread sums are compensated (Kahan) in the data precision, the
+// cross-thread sum is FP64 and deterministic.
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(pf::kReduceBlock) zero_mode_kernel(const T* __restrict__ g, int nx, int ny, int nz,
+                                                                      int trap_x, int trap_y, int trap_z,
+                                                                      pf::Reduce R, double* out) {
+  const long long N = (long long)nx * ny * nz;
+  T s = T(0), c = T(0);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx);
+    const long long r = i / nx;
+    const int y = (int)(r % ny), z = (int)(r / ny);
+    T w = T(1);
+    if (trap_x && (x == 0 || x == nx - 1)) w *= T(0.5);
+    if (trap_y && (y == 0 || y == ny - 1)) w *= T(0.5);
+    if (trap_z && (z == 0 || z == nz - 1)) w *= T(0.5);
+    const T yv = w * g[i] - c;
+    const T t = s + yv;
+    c = (t - s) - yv;
+    s = t;
+  }
+  const double v[1] = {(double)s - (double)c};
+  double* const d[1] = {out};
+  pf::grid_sum<1>(v, R, d);
+}
+
+}  // namespace
+
+extern "C" int poisfft_zero_mode_mean(poisfft_plan* p, const void* g, double* mean, void* stream) {
+  if (!p || !g || !mean) return POISFFT_ERR_INVALID_ARG;
+  if (!p->singular) return POISFFT_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return POISFFT_ERR_CUDA;
+  const unsigned nb = (unsigned)std::max<long long>(1, std::min<long long>((N + 255) / 256, (long long)sms * 8));
+  if (!p->zm) {
+    if (cudaMalloc(&p->zm, (1 + (size_t)sms * 8) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&p->zm_count, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(p->zm_count, 0, sizeof(unsigned)) != cudaSuccess) {
+      cudaGetLastError();
+      return POISFFT_ERR_ALLOC;
+    }
+  }
+  const pf::Reduce R{p->zm + 1, p->zm_count};
+  const int tx = p->axes[0].bc == POISFFT_NR, ty = p->dims >= 2 && p->axes[1].bc == POISFFT_NR,
+            tz = p->dims >= 3 && p->axes[2].bc == POISFFT_NR;
+  if (p->esize == 4)
+    zero_mode_kernel<float><<<nb, pf::kReduceBlock, 0, st>>>(static_cast<const float*>(g), p->nx, p->ny, p->nz, tx,
+                                                             ty, tz, R, p->zm);
+  else
+    zero_mode_kernel<double><<<nb, pf::kReduceBlock, 0, st>>>(static_cast<const double*>(g), p->nx, p->ny, p->nz,
+                                                              tx, ty, tz, R, p->zm);
+  double sum = 0.0;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&sum, p->zm, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return POISFFT_ERR_CUDA;
+  double wsum = 1.0;
+  const int nn[3] = {p->nx, p->ny, p->nz};
+  for (int a = 0; a < 3; a++) wsum *= (a < p->dims && p->axes[a].bc == POISFFT_NR) ? nn[a] - 1.0 : (double)nn[a];
+  *mean = sum / wsum;
+  return POISFFT_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Solve without device allocation

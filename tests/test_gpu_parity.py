@@ -313,3 +313,22 @@ def test_bluestein_large_2d_batch_case(pb):
     """A batch problem that dominated the direct-DFT timings: y = DST-I with
     n = 1800 (extension 2 * 1801)."""
     check(pb, (1800, 1792), (W.DS, W.DR), W.FD2, "f32", seed=18, method="fft")
+
+
+@pytest.mark.parametrize("n,bcs", [((64, 48, 40), (W.P, W.P, W.NS)), ((33, 20, 17), (W.NR, W.P, W.NS)),
+                                   ((17, 9, 12), (W.NR, W.NR, W.NR)), ((256, 128), (W.NS, W.NR))])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_zero_mode_mean_fp64(pb, n, bcs, dtype):
+    shape = tuple(reversed(n))
+    npdt = np.float32 if dtype == "f32" else np.float64
+    g = (W.normal(shape, 41) + 0.375).astype(npdt)
+    ref = O.weighted_mean(g.astype(np.float64), bcs)
+    with pb.Plan(n, tuple(1.0 for _ in n), bcs, W.FD2, pb.F32 if dtype == "f32" else pb.F64) as plan:
+        got = plan.zero_mode_mean(torch.from_numpy(g).cuda())
+    assert abs(got - ref) <= (1e-12 if dtype == "f64" else 1e-7) * np.max(np.abs(g))
+
+
+def test_zero_mode_mean_rejects_nonsingular(pb):
+    with pb.Plan((16, 8, 8), (1.0, 1.0, 1.0), (W.P, W.DS, W.NS), W.FD2, pb.F32) as plan:
+        with pytest.raises(pb.PoisFFTError):
+            plan.zero_mode_mean(torch.zeros(16 * 8 * 8, device="cuda"))
