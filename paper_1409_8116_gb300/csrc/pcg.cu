@@ -360,6 +360,134 @@ __global__ void __launch_bounds__(kBlock) mx_dir_kernel(float* __restrict__ p, c
   GRID_STRIDE(i, N) p[i] = first ? scale * zA[i] : scale * zA[i] + beta * p[i];
 }
 
+// ---- mixed iteration, four cells per thread (nx a multiple of 4) ----------
+// The same arithmetic as the kernels above on 128-bit loads: every thread
+// keeps four cells' loads in flight, which the scalar forms cannot (they
+// stall on memory latency at a third to a half of the DRAM bandwidth).
+
+__device__ __forceinline__ float4 ld4(const float* p, unsigned i4) { return reinterpret_cast<const float4*>(p)[i4]; }
+__device__ __forceinline__ void st4(float* p, unsigned i4, float4 v) { reinterpret_cast<float4*>(p)[i4] = v; }
+__device__ __forceinline__ float get(const float4& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w)); }
+
+// q = K p for cells 4 i4 .. 4 i4 + 3 (one x row segment); dot += p.q
+__global__ void __launch_bounds__(kBlock) apply4_kernel(const float* __restrict__ p, Faces<float> F,
+                                                        const float* __restrict__ a, Grid G, float* __restrict__ q,
+                                                        Reduce R, double* dot, const int* done) {
+  if (gated(done)) return;
+  const unsigned N4 = G.N / 4, sy4 = (unsigned)G.nx / 4, sz4 = sy4 * (unsigned)G.ny;
+  float part = 0.f;
+  GRID_STRIDE(i4, N4) {
+    const unsigned i = 4 * i4;
+    int x, y, z;
+    cell_xyz(G, i, x, y, z);
+    const float4 pc = ld4(p, i4);
+    const float pv[4] = {pc.x, pc.y, pc.z, pc.w};
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    // x faces: lower faces of the four cells, and the one above the last
+    const float4 fx = ld4(F.c[0], i4);
+    const bool has_l = x > 0, has_r = x + 4 < G.nx;
+    const float pl = has_l ? p[i - 1] : 0.f;
+    const float pr = has_r ? p[i + 4] : 0.f;
+    const float fr = has_r ? F.c[0][i + 4] : a[i + 3] * G.fidx2;
+    {
+      const float fl[5] = {fx.x, fx.y, fx.z, fx.w, fr};
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const float vl = k > 0 ? pv[k - 1] : (has_l ? pl : -pv[0]);
+        const float vh = k < 3 ? pv[k + 1] : (has_r ? pr : -pv[3]);
+        acc[k] += fl[k + 1] * (vh - pv[k]) - fl[k] * (pv[k] - vl);
+      }
+    }
+    // y and z faces: whole float4 rows of the neighbouring lines
+#pragma unroll
+    for (int d = 1; d < 3; d++) {
+      const unsigned st = d == 1 ? sy4 : sz4;
+      const bool lo = (d == 1 ? y : z) > 0;
+      const bool hi = (d == 1 ? y < G.ny - 1 : z < G.nz - 1);
+      const float4 fl = ld4(F.c[d], i4);
+      const float4 plo = lo ? ld4(p, i4 - st) : pc;
+      const float4 phi = hi ? ld4(p, i4 + st) : pc;
+      float4 fh;
+      if (hi) {
+        fh = ld4(F.c[d], i4 + st);
+      } else {
+        const float4 av = ld4(a, i4);
+        const float s2 = d == 1 ? G.fidy2 : G.fidz2;
+        fh = make_float4(av.x * s2, av.y * s2, av.z * s2, av.w * s2);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const float vk = pv[k];
+        const float vl = lo ? get(plo, k) : -vk;
+        const float vh = hi ? get(phi, k) : -vk;
+        acc[k] += get(fh, k) * (vh - vk) - get(fl, k) * (vk - vl);
+      }
+    }
+    const float4 qv = make_float4(-acc[0], -acc[1], -acc[2], -acc[3]);
+    st4(q, i4, qv);
+    part += pc.x * qv.x + pc.y * qv.y + pc.z * qv.z + pc.w * qv.w;
+  }
+  if (dot) {
+    const double v[1] = {(double)part};
+    double* const d[1] = {dot};
+    grid_sum<1>(v, R, d);
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) mx_update4_kernel(float* __restrict__ e, float* __restrict__ r,
+                                                            const float* __restrict__ p,
+                                                            const float* __restrict__ q, Scalars* S, Reduce R, int s,
+                                                            int sp, unsigned N4) {
+  if (gated(&S->done)) return;
+  const float alpha = (float)(S->rz[sp] / S->pq[s]);
+  float v = 0.f;
+  GRID_STRIDE(i4, N4) {
+    const float4 ev = ld4(e, i4), rv = ld4(r, i4), pv = ld4(p, i4), qv = ld4(q, i4);
+    const float4 en = make_float4(ev.x + alpha * pv.x, ev.y + alpha * pv.y, ev.z + alpha * pv.z, ev.w + alpha * pv.w);
+    const float4 rn = make_float4(rv.x - alpha * qv.x, rv.y - alpha * qv.y, rv.z - alpha * qv.z, rv.w - alpha * qv.w);
+    st4(e, i4, en);
+    st4(r, i4, rn);
+    v += rn.x * rn.x + rn.y * rn.y + rn.z * rn.z + rn.w * rn.w;
+  }
+  const double vv[1] = {(double)v};
+  double* const d[1] = {&S->rr[s]};
+  grid_sum<1>(vv, R, d);
+}
+
+__global__ void __launch_bounds__(kBlock) mx_precond4_kernel(const float* __restrict__ r,
+                                                             const float* __restrict__ zA,
+                                                             const float* __restrict__ zB, double scale, Scalars* S,
+                                                             Reduce R, int s, int first, unsigned N4) {
+  if (gated(&S->done)) return;
+  float v = 0.f, w = 0.f;
+  GRID_STRIDE(i4, N4) {
+    const float4 rv = ld4(r, i4), za = ld4(zA, i4);
+    v += rv.x * za.x + rv.y * za.y + rv.z * za.z + rv.w * za.w;
+    if (first) {
+      w += rv.x * za.x + rv.y * za.y + rv.z * za.z + rv.w * za.w;
+    } else {
+      const float4 zb = ld4(zB, i4);
+      w += rv.x * (za.x - zb.x) + rv.y * (za.y - zb.y) + rv.z * (za.z - zb.z) + rv.w * (za.w - zb.w);
+    }
+  }
+  const double vw[2] = {scale * (double)v, scale * (double)w};
+  double* const d[2] = {&S->rz[s], &S->rdz[s]};
+  grid_sum<2>(vw, R, d);
+}
+
+__global__ void __launch_bounds__(kBlock) mx_dir4_kernel(float* __restrict__ p, const float* __restrict__ zA,
+                                                         float scale, Scalars* S, int s, int sp, int first,
+                                                         unsigned N4) {
+  if (gated(&S->done)) return;
+  const float beta = first ? 0.f : (float)(S->rdz[s] / S->rz[sp]);
+  GRID_STRIDE(i4, N4) {
+    const float4 za = ld4(zA, i4);
+    const float4 pv = first ? make_float4(0.f, 0.f, 0.f, 0.f) : ld4(p, i4);
+    st4(p, i4, make_float4(scale * za.x + beta * pv.x, scale * za.y + beta * pv.y, scale * za.z + beta * pv.z,
+                           scale * za.w + beta * pv.w));
+  }
+}
+
 // ---- features of the learned initial guess --------------------------------
 
 // Sums that set the feature scales: r.r, z.z, sum log a, sum (log a)^2
@@ -595,6 +723,7 @@ int solve_mixed(poisfft_pcg* s, double* phi, const double* g, double tol, int ma
   const Faces<float> F32 = faces_of<float>(s);
   int* done = &s->S->done;
   int* rel_flag = &s->S->reliable;
+  const bool vec4 = s->G.nx % 4 == 0;  // 128-bit rows (device buffers are 256-byte aligned)
   float* zA = s->z32;   // preconditioner output for the current residual
   float* zB = s->zb32;  // ... for the previous one
   int64_t precond = 0;
@@ -602,8 +731,13 @@ int solve_mixed(poisfft_pcg* s, double* phi, const double* g, double tol, int ma
     int rc = poisfft_solve(s->plan, zA, s->r32, stream);
     if (rc != POISFFT_OK) return rc;
     precond++;
-    mx_precond_kernel<<<nb, kBlock, 0, st>>>(s->r32, zA, zB, scale, s->S, R, slot, first, N);
-    mx_dir_kernel<<<nb, kBlock, 0, st>>>(s->p32, zA, (float)scale, s->S, slot, sp, first, N);
+    if (vec4) {
+      mx_precond4_kernel<<<nb, kBlock, 0, st>>>(s->r32, zA, zB, scale, s->S, R, slot, first, N / 4);
+      mx_dir4_kernel<<<nb, kBlock, 0, st>>>(s->p32, zA, (float)scale, s->S, slot, sp, first, N / 4);
+    } else {
+      mx_precond_kernel<<<nb, kBlock, 0, st>>>(s->r32, zA, zB, scale, s->S, R, slot, first, N);
+      mx_dir_kernel<<<nb, kBlock, 0, st>>>(s->p32, zA, (float)scale, s->S, slot, sp, first, N);
+    }
     std::swap(zA, zB);
     return cudaGetLastError() == cudaSuccess ? POISFFT_OK : POISFFT_ERR_CUDA;
   };
@@ -618,8 +752,13 @@ int solve_mixed(poisfft_pcg* s, double* phi, const double* g, double tol, int ma
   if ((rc = publish(s, 0, st)) != POISFFT_OK) return rc;
   for (int k = 1; k <= maxit; k++) {
     const int sl = k & 1, sp = sl ^ 1;
-    apply_kernel<float><<<nb, kBlock, 0, st>>>(s->p32, F32, s->a, s->G, s->q32, R, &s->S->pq[sl], done);
-    mx_update_kernel<<<nb, kBlock, 0, st>>>(s->e, s->r32, s->p32, s->q32, s->S, R, sl, sp, N);
+    if (vec4) {
+      apply4_kernel<<<nb, kBlock, 0, st>>>(s->p32, F32, s->a, s->G, s->q32, R, &s->S->pq[sl], done);
+      mx_update4_kernel<<<nb, kBlock, 0, st>>>(s->e, s->r32, s->p32, s->q32, s->S, R, sl, sp, N / 4);
+    } else {
+      apply_kernel<float><<<nb, kBlock, 0, st>>>(s->p32, F32, s->a, s->G, s->q32, R, &s->S->pq[sl], done);
+      mx_update_kernel<<<nb, kBlock, 0, st>>>(s->e, s->r32, s->p32, s->q32, s->S, R, sl, sp, N);
+    }
     mx_check_kernel<<<1, 1, 0, st>>>(s->S, sl, k, tol, kReliableDelta);
     mx_axpy_kernel<<<nb, kBlock, 0, st>>>(phi, s->e, done, rel_flag, N);
     mx_resid_kernel<<<nb, kBlock, 0, st>>>(phi, g, F64, s->a, s->G, s->r32, s->S, R, rel_flag, 0);
