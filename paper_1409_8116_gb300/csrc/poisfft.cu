@@ -1072,20 +1072,22 @@ template <typename T>
 __global__ void __launch_bounds__(pf::kReduceBlock) zero_mode_kernel(const T* __restrict__ g, int nx, int ny, int nz,
                                                                       int trap_x, int trap_y, int trap_z,
                                                                       pf::Reduce R, double* out) {
-  const long long N = (long long)nx * ny * nz;
+  // blocks take whole x rows: the y/z weight is fixed per row, x is coalesced
+  const long long rows = (long long)ny * nz;
   T s = T(0), c = T(0);
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(i % nx);
-    const long long r = i / nx;
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
     const int y = (int)(r % ny), z = (int)(r / ny);
-    T w = T(1);
-    if (trap_x && (x == 0 || x == nx - 1)) w *= T(0.5);
-    if (trap_y && (y == 0 || y == ny - 1)) w *= T(0.5);
-    if (trap_z && (z == 0 || z == nz - 1)) w *= T(0.5);
-    const T yv = w * g[i] - c;
-    const T t = s + yv;
-    c = (t - s) - yv;
-    s = t;
+    T wr = T(1);
+    if (trap_y && (y == 0 || y == ny - 1)) wr *= T(0.5);
+    if (trap_z && (z == 0 || z == nz - 1)) wr *= T(0.5);
+    const T* row = g + r * nx;
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+      const T w = (trap_x && (x == 0 || x == nx - 1)) ? T(0.5) * wr : wr;
+      const T yv = w * row[x] - c;
+      const T t = s + yv;
+      c = (t - s) - yv;
+      s = t;
+    }
   }
   const double v[1] = {(double)s - (double)c};
   double* const d[1] = {out};
