@@ -196,10 +196,16 @@ def test_solve_host_buffers(pb):
         ph = torch.empty_like(gh).pin_memory()
         plan.solve_host(ph, gh, torch.cuda.current_stream())
         assert O.rel_max_error(ph.numpy(), ref) < 1e-5
-        # pageable numpy buffers work too
+        # pageable numpy buffers work too (staged copies)
         out = np.empty_like(g)
         plan.solve_host(out, g)
         assert O.rel_max_error(out, ref) < 1e-5
+        # bit-identical to the solve on device buffers
+        gd = gh.cuda()
+        pd = torch.empty_like(gd)
+        plan.solve(pd, gd, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert torch.equal(pd.cpu(), ph)
 
 
 def test_nonzero_mean_rhs_singular(pb):
