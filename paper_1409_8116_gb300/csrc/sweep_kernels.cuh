@@ -145,10 +145,10 @@ __device__ __forceinline__ T eigen_factor(const StridedArgs& a, const T* lin, co
   return T(a.scale) / den;
 }
 
-template <typename T>
 // Two CTAs per SM: the register cap (128) makes the compiler spill a few
 // kilobytes per thread, but the doubled occupancy more than pays for it
 // (512 uneven batch problems: 153 -> 135 ms of summed solve time).
+template <typename T>
 __global__ void __launch_bounds__(kThreads, 2) strided_sweep_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                  const StridedArgs a) {
   constexpr int EMAX = Emax<T>::value;
