@@ -14,7 +14,8 @@ poisfft_solve_host (host buffers; H2D + solve + D2H inside the timed
 region); `roofline` covers the launch with the largest share of the step
 time, timed live with per-launch CUDA events recorded by the library on the
 same stream; `cpu_baseline` is the FP64 oracle on a bounded sample of the
-same workload on this machine's host cores.
+same workload on this machine's host cores; `cufft_comparison` times cuFFT
+(through torch.fft, all axes periodic) on the same field for context.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                   [--impl ours|reference] [--no-check]
@@ -79,6 +80,7 @@ def parse():
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 error check of the solution")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer (e2e) measurement")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison")
     return ap.parse_args()
 
 
@@ -236,6 +238,38 @@ def run_reference(args):
     return 0
 
 
+def cufft_comparison(g, warmup, steps):
+    """The same field through cuFFT (torch.fft): 3D R2C, a pointwise multiply
+    by a precomputed real factor (the divide), 3D C2R.  cuFFT has no DCT, so
+    every axis is treated as periodic: the same class of work as the
+    product's solve, not the same boundary conditions.  Device-timed with
+    CUDA events; None when the field does not fit beside cuFFT's workspace."""
+    import torch
+
+    try:
+        nz, ny, nx = g.shape
+        fac = torch.rand((nz, ny, nx // 2 + 1), device=g.device, dtype=torch.float32)
+        out = None
+        for _ in range(max(1, warmup)):
+            out = torch.fft.irfftn(torch.fft.rfftn(g) * fac, s=(nz, ny, nx))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            out = torch.fft.irfftn(torch.fft.rfftn(g) * fac, s=(nz, ny, nx))
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        del out, fac
+        torch.cuda.empty_cache()
+        return {"ms_per_solve": ms, "points_per_s": nx * ny * nz / (ms / 1e3), "steps": steps,
+                "what": "torch.fft (cuFFT) rfftn, multiply by a real factor, irfftn on the same FP32 field; "
+                        "all axes periodic (cuFFT has no DCT)"}
+    except RuntimeError as exc:  # out of memory next to the plan's buffers
+        torch.cuda.empty_cache()
+        return {"unavailable": str(exc).splitlines()[0][:200]}
+
+
 def plan_singular(bcs):
     """Every axis periodic or Neumann: the solve removes the zero mode."""
     return all(b in (0, 3, 4) for b in bcs)
@@ -343,6 +377,11 @@ def run_ours(args):
         e2e_same = bool(torch.equal(ph.view(-1)[::stride], phi.cpu().view(-1)[::stride]))
         del gh, ph
 
+    # ---- library comparison (not part of the product): cuFFT through torch.fft
+    cufft = None
+    if rank == 0 and not args.no_cufft:
+        cufft = cufft_comparison(g, args.warmup, min(args.steps, 10))
+
     # ---- accuracy against the FP64 oracle (not timed)
     err = None
     if not args.no_check and rank == 0:
@@ -372,7 +411,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if f64 else "f32", "data": "synthetic",
             "config": workload_config(args.workload, spec),
-            "max_rel_err_vs_fp64": err, "zero_mode": zero_mode,
+            "max_rel_err_vs_fp64": err, "zero_mode": zero_mode, "cufft_comparison": cufft,
             "hbm_frac_step": step_bytes * args.steps / (ms_max / 1e3) / 1e9 / peak,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
