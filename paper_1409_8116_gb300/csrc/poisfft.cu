@@ -445,7 +445,6 @@ size_t strided_per_col(const poisfft_plan* p, int axis, int rows_alloc) {
 // x sweep configuration
 int plan_x_sweep(poisfft_plan* p, int mode, SweepLaunch& L) {
   AxisPlan& ax = p->axes[0];
-  const int M = ax.d.fft.M;
   const size_t cx = 2 * p->esize;
   const long long nrows = (long long)p->ny * p->nz;
   const long long pairs = (nrows + 1) / 2;
