@@ -222,7 +222,9 @@ int poisfft_batch_destroy(poisfft_batch* batch);
  * poisfft_pcg_stats: out[0] iterations, out[1] FP64 (true) residual
  *   evaluations, out[2] preconditioner solves, out[3] precision of the last
  *   poisfft_pcg_solve.
- * poisfft_pcg_apply: out = -(A in) (device doubles), the operator alone. */
+ * poisfft_pcg_apply: out = -(A in) (device doubles), the operator alone.
+ * Device arrays must be aligned to their element size
+ * (POISFFT_ERR_MISALIGNED otherwise). */
 typedef enum { POISFFT_PCG_F64 = 0, POISFFT_PCG_MIXED = 1 } poisfft_pcg_precision;
 typedef struct poisfft_pcg poisfft_pcg;
 int poisfft_pcg_create(poisfft_pcg** out, const int64_t n[3], const double L[3], const float* a, double a_ref);
@@ -275,7 +277,9 @@ int poisfft_pcg_set_coefficient(poisfft_pcg* pcg, const float* a, double a_ref);
  * poisfft_pcg_learned_guess: phi (device doubles, overwritten) = phi0 +
  *   rms(phi0) y for g, then `corrections` times: r = g - A phi (FP64),
  *   phi += the same construction for r.  The network must have batch 1 and
- *   the PCG's grid.  Synchronises nothing; pass phi to poisfft_pcg_solve. */
+ *   the PCG's grid.  Synchronises nothing; pass phi to poisfft_pcg_solve.
+ * Device arrays must be aligned to their element size
+ * (POISFFT_ERR_MISALIGNED otherwise). */
 typedef struct poisfft_sno poisfft_sno;
 int64_t poisfft_sno_num_params(int channels, int modes, int layers);
 int poisfft_sno_create(poisfft_sno** out, const int64_t n[3], int batch, int channels, int modes, int layers,

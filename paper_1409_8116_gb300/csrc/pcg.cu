@@ -779,6 +779,12 @@ int solve_mixed(poisfft_pcg* s, double* phi, const double* g, double tol, int ma
 
 }  // namespace
 
+namespace {
+// device arrays must be aligned to their element size (a misaligned pointer
+// would fault in the kernels, so it is refused here)
+template <typename T> bool aligned(const T* p) { return p == nullptr || (uintptr_t)p % sizeof(T) == 0; }
+}  // namespace
+
 extern "C" {
 
 int poisfft_pcg_create(poisfft_pcg** out, const int64_t n[3], const double L[3], const float* a, double a_ref) {
@@ -849,6 +855,7 @@ int poisfft_pcg_create(poisfft_pcg** out, const int64_t n[3], const double L[3],
 
 int poisfft_pcg_apply(poisfft_pcg* s, double* out, const double* in, void* stream) {
   if (!s || !out || !in) return POISFFT_ERR_INVALID_ARG;
+  if (!aligned(out) || !aligned(in)) return POISFFT_ERR_MISALIGNED;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   apply_kernel<double><<<s->nb, kBlock, 0, st>>>(in, faces_of<double>(s), s->a, s->G, out,
                                                  Reduce{s->part, s->count}, nullptr, nullptr);
@@ -858,6 +865,7 @@ int poisfft_pcg_apply(poisfft_pcg* s, double* out, const double* in, void* strea
 int poisfft_pcg_solve(poisfft_pcg* s, double* phi, const double* g, double tol, int maxit, int precision, int* iters,
                       double* relres, void* stream) {
   if (!s || !phi || !g || maxit < 0 || !(tol >= 0.0)) return POISFFT_ERR_INVALID_ARG;
+  if (!aligned(phi) || !aligned(g)) return POISFFT_ERR_MISALIGNED;
   if (precision == POISFFT_PCG_F64) return solve_f64(s, phi, g, tol, maxit, iters, relres, stream);
   if (precision == POISFFT_PCG_MIXED) return solve_mixed(s, phi, g, tol, maxit, iters, relres, stream);
   return POISFFT_ERR_INVALID_ARG;
@@ -877,6 +885,7 @@ int poisfft_pcg_set_coefficient(poisfft_pcg* s, const float* a, double a_ref) {
 int poisfft_pcg_features(poisfft_pcg* s, const double* g, const double* phi, float* feats, float* target,
                          void* stream) {
   if (!s || !g || !feats) return POISFFT_ERR_INVALID_ARG;
+  if (!aligned(g) || !aligned(phi) || !aligned(feats) || !aligned(target)) return POISFFT_ERR_MISALIGNED;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int rc = learned_features(s, g, 0, st);
   if (rc != POISFFT_OK) return rc;
@@ -889,6 +898,7 @@ int poisfft_pcg_features(poisfft_pcg* s, const double* g, const double* phi, flo
 int poisfft_pcg_learned_guess(poisfft_pcg* s, poisfft_sno* sno, double* phi, const double* g, int corrections,
                               void* stream) {
   if (!s || !sno || !phi || !g || corrections < 0) return POISFFT_ERR_INVALID_ARG;
+  if (!aligned(phi) || !aligned(g)) return POISFFT_ERR_MISALIGNED;
   int64_t info[8];
   if (poisfft_sno_info(sno, info) != POISFFT_OK) return POISFFT_ERR_INVALID_ARG;
   if (info[0] != s->G.nx || info[1] != s->G.ny || info[2] != s->G.nz || info[3] != 1) return POISFFT_ERR_INVALID_ARG;

@@ -630,6 +630,10 @@ int upload_matrix(float** dst, const std::vector<double>& h) {
 
 }  // namespace
 
+namespace {
+template <typename T> bool aligned(const T* p) { return p == nullptr || (uintptr_t)p % sizeof(T) == 0; }
+}  // namespace
+
 extern "C" {
 
 int64_t poisfft_sno_num_params(int channels, int modes, int layers) {
@@ -754,6 +758,7 @@ int poisfft_sno_get_params(const poisfft_sno* s, float* theta) {
 
 int poisfft_sno_forward(poisfft_sno* s, float* y, const float* feats, void* stream) {
   if (!s || !y || !feats) return POISFFT_ERR_INVALID_ARG;
+  if (!aligned(y) || !aligned(feats)) return POISFFT_ERR_MISALIGNED;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const Dims& D = s->D;
   const Layout& O = s->lay;
@@ -784,6 +789,7 @@ int poisfft_sno_forward(poisfft_sno* s, float* y, const float* feats, void* stre
 int poisfft_sno_backward(poisfft_sno* s, float* grad, const float* dy, const float* feats, void* stream) {
   if (!s || !grad || !dy || !feats) return POISFFT_ERR_INVALID_ARG;
   if (!s->train) return POISFFT_ERR_INVALID_ARG;
+  if (!aligned(grad) || !aligned(dy) || !aligned(feats)) return POISFFT_ERR_MISALIGNED;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const Dims& D = s->D;
   const Layout& O = s->lay;
@@ -827,6 +833,7 @@ int poisfft_sno_backward(poisfft_sno* s, float* grad, const float* dy, const flo
 
 int poisfft_sno_loss(poisfft_sno* s, const float* y, const float* t, float* dy, double* loss, void* stream) {
   if (!s || !y || !t) return POISFFT_ERR_INVALID_ARG;
+  if (!aligned(y) || !aligned(t) || !aligned(dy)) return POISFFT_ERR_MISALIGNED;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const long long n = (long long)s->D.B * s->D.N;
   const unsigned gb = grid_for(n, s->sms);
@@ -845,6 +852,7 @@ int poisfft_sno_loss(poisfft_sno* s, const float* y, const float* t, float* dy, 
 int poisfft_sno_adam(poisfft_sno* s, const float* grad, double lr, double beta1, double beta2, double eps, int step,
                      void* stream) {
   if (!s || !grad || !s->train || step < 1) return POISFFT_ERR_INVALID_ARG;
+  if (!aligned(grad)) return POISFFT_ERR_MISALIGNED;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const double lr_t = lr * sqrt(1.0 - pow(beta2, step)) / (1.0 - pow(beta1, step));
   const long long P = s->lay.total;

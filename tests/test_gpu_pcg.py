@@ -162,3 +162,9 @@ def test_invalid_arguments(pb):
             s.solve(x, x, precision=7)
         with pytest.raises(pb.PoisFFTError):
             s.solve(x, x, tol=-1.0)
+        # misaligned device pointers are refused before any launch
+        with pytest.raises(pb.PoisFFTError) as e:
+            s.solve(x.data_ptr() + 4, x.data_ptr())
+        assert e.value.status == pb.ERR_MISALIGNED
+        with pytest.raises(pb.PoisFFTError):
+            s.apply(x.data_ptr(), x.data_ptr() + 4)
