@@ -72,10 +72,10 @@ typedef struct poisfft_plan poisfft_plan;  /* opaque; owned by the library */
  * padding) and FP64-derived tables on the current CUDA device.  All
  * argument checks happen before any CUDA call, so argument errors are
  * reported even without a GPU.
- * FP32 plans with a periodic x axis, y/z axes periodic or staggered
- * (Dirichlet or Neumann) and every length in {64, 128, 256, 512, 1024} use
- * specialised two-pass kernels; all others use the general mixed-radix
- * kernels.  Setting the environment variable POISFFT_FORCE_GENERIC=1 at plan
+ * FP32 plans of 2 or 3 dimensions with every length in {64, 128, 256, 512,
+ * 1024} use specialised two-pass kernels when x is periodic and y/z are
+ * periodic or staggered (Dirichlet or Neumann), or when x, y and z are all
+ * staggered; all others use the general mixed-radix kernels.  Setting the environment variable POISFFT_FORCE_GENERIC=1 at plan
  * creation selects the general kernels for every plan (testing aid). */
 int poisfft_plan_create(poisfft_plan** out, int dims, const int64_t n[], const double L[],
                         const int bc[], int approx, int dtype);
