@@ -193,13 +193,23 @@ struct ColTile {
   int w, lw;
   __device__ __forceinline__ int idx(int m, int c) const { return m * w + c; }
   // split a flat index over (lines of length len) x (w columns)
-  __device__ __forceinline__ void split(int b, int /*len*/, int& i, int& c) const { c = b & (w - 1); i = b >> lw; }
+  __device__ __forceinline__ void split(int b, const FastDiv& /*len*/, int& i, int& c) const {
+    c = b & (w - 1);
+    i = b >> lw;
+  }
 };
-// Row tile of the contiguous sweep: element (m, line) at line*ld + m.
+// Row tile of the contiguous sweep: element (m, line) at line*ld + m + (m >> sh),
+// one padding element after every 2^sh (one 128-byte bank sweep of complex
+// values).  Without it the digit-reversed gathers of the post-processing and
+// the butterflies of the last passes, whose threads step by a power of two,
+// meet in one bank; ld >= len + (len >> sh).
 struct RowTile {
-  int ld;
-  __device__ __forceinline__ int idx(int m, int c) const { return c * ld + m; }
-  __device__ __forceinline__ void split(int b, int len, int& i, int& c) const { c = b / len; i = b - c * len; }
+  int ld, sh;
+  __device__ __forceinline__ int idx(int m, int c) const { return c * ld + m + (m >> sh); }
+  __device__ __forceinline__ void split(int b, const FastDiv& len, int& i, int& c) const {
+    c = (int)fdiv((uint32_t)b, len);
+    i = b - c * (int)len.d;
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -214,15 +224,15 @@ struct RowTile {
 // sum_i s_i L_i/R_i (digit reversal); the post-processing gathers read it
 // through the `perm` table.
 template <typename T, int R, bool INV, class LAY>
-__device__ __noinline__ void dif_pass(cx<T>* __restrict__ buf, const LAY lay, int M, int ncol, int L,
-                                      const cx<T>* __restrict__ tw) {
-  const int Lr = L / R;
-  const int nbl = M / R;
-  const int nb = nbl * ncol;
+__device__ __noinline__ void dif_pass(cx<T>* __restrict__ buf, const LAY lay, int M, int ncol, const FastDiv dnbl,
+                                      const FastDiv dLr, const cx<T>* __restrict__ tw) {
+  const int Lr = (int)dLr.d;
+  const int L = Lr * R;
+  const int nb = (M / R) * ncol;
   for (int b = threadIdx.x; b < nb; b += kThreads) {
     int t, c;
-    lay.split(b, nbl, t, c);
-    const int blk = t / Lr;
+    lay.split(b, dnbl, t, c);
+    const int blk = (int)fdiv((uint32_t)t, dLr);
     const int j = t - blk * Lr;
     const int base = blk * L + j;
     cx<T> u[R];
@@ -247,16 +257,17 @@ __device__ __noinline__ void dif_pass(cx<T>* __restrict__ buf, const LAY lay, in
 // is copied back afterwards.  O(R) work per point, no per-thread arrays.
 template <typename T, bool INV, class LAY>
 __device__ __noinline__ void dif_pass_generic(cx<T>* __restrict__ buf, cx<T>* __restrict__ scratch, const LAY lay,
-                                              int M, int ncol, int R, int L, const cx<T>* __restrict__ tw,
-                                              const cx<T>* __restrict__ roots) {
-  const int Lr = L / R;
-  const int total = M * ncol;
+                                              const FastDiv dM, int ncol, int R, const FastDiv dL, const FastDiv dLr,
+                                              const cx<T>* __restrict__ tw, const cx<T>* __restrict__ roots) {
+  const int Lr = (int)dLr.d;
+  const int L = (int)dL.d;
+  const int total = (int)dM.d * ncol;
   for (int e = threadIdx.x; e < total; e += kThreads) {
     int pos, c;
-    lay.split(e, M, pos, c);
-    const int blk = pos / L;
+    lay.split(e, dM, pos, c);
+    const int blk = (int)fdiv((uint32_t)pos, dL);
     const int rem = pos - blk * L;
-    const int s = rem / Lr;
+    const int s = (int)fdiv((uint32_t)rem, dLr);
     const int j = rem - s * Lr;
     const int base = blk * L + j;
     cx<T> acc = czero<T>();
@@ -277,7 +288,7 @@ __device__ __noinline__ void dif_pass_generic(cx<T>* __restrict__ buf, cx<T>* __
   __syncthreads();
   for (int e = threadIdx.x; e < total; e += kThreads) {
     int pos, c;
-    lay.split(e, M, pos, c);
+    lay.split(e, dM, pos, c);
     buf[lay.idx(pos, c)] = scratch[lay.idx(pos, c)];
   }
   __syncthreads();
@@ -288,15 +299,15 @@ __device__ __noinline__ void dif_pass_generic(cx<T>* __restrict__ buf, cx<T>* __
 // writes output s back to block*L + j + s*(L/R).  Run in the reverse order
 // of the DIF passes, DIT takes the DIF output arrangement to natural order.
 template <typename T, int R, bool INV, class LAY>
-__device__ __noinline__ void dit_pass(cx<T>* __restrict__ buf, const LAY lay, int M, int ncol, int L,
-                                      const cx<T>* __restrict__ tw) {
-  const int Lr = L / R;
-  const int nbl = M / R;
-  const int nb = nbl * ncol;
+__device__ __noinline__ void dit_pass(cx<T>* __restrict__ buf, const LAY lay, int M, int ncol, const FastDiv dnbl,
+                                      const FastDiv dLr, const cx<T>* __restrict__ tw) {
+  const int Lr = (int)dLr.d;
+  const int L = Lr * R;
+  const int nb = (M / R) * ncol;
   for (int b = threadIdx.x; b < nb; b += kThreads) {
     int t, c;
-    lay.split(b, nbl, t, c);
-    const int blk = t / Lr;
+    lay.split(b, dnbl, t, c);
+    const int blk = (int)fdiv((uint32_t)t, dLr);
     const int j = t - blk * Lr;
     const int base = blk * L + j;
     cx<T> u[R];
@@ -322,15 +333,15 @@ __device__ __forceinline__ void run_passes_dit(cx<T>* buf, const LAY lay, const 
                                                const cx<T>* __restrict__ tables) {
   for (int ps = f.npass - 1; ps >= 0; ps--) {
     const int R = f.radix[ps];
-    const int L = f.p[ps];
+    const FastDiv dNb = f.dNb[ps], dLr = f.dLr[ps];
     const cx<T>* tw = tables + f.tw_off[ps];
     switch (R) {
-      case 2: dit_pass<T, 2, INV>(buf, lay, f.M, ncol, L, tw); break;
-      case 4: dit_pass<T, 4, INV>(buf, lay, f.M, ncol, L, tw); break;
-      case 8: dit_pass<T, 8, INV>(buf, lay, f.M, ncol, L, tw); break;
-      case 16: dit_pass<T, 16, INV>(buf, lay, f.M, ncol, L, tw); break;
+      case 2: dit_pass<T, 2, INV>(buf, lay, f.M, ncol, dNb, dLr, tw); break;
+      case 4: dit_pass<T, 4, INV>(buf, lay, f.M, ncol, dNb, dLr, tw); break;
+      case 8: dit_pass<T, 8, INV>(buf, lay, f.M, ncol, dNb, dLr, tw); break;
+      case 16: dit_pass<T, 16, INV>(buf, lay, f.M, ncol, dNb, dLr, tw); break;
       default:
-        if constexpr (EMAX >= 32) dit_pass<T, 32, INV>(buf, lay, f.M, ncol, L, tw);
+        if constexpr (EMAX >= 32) dit_pass<T, 32, INV>(buf, lay, f.M, ncol, dNb, dLr, tw);
         break;
     }
   }
@@ -341,21 +352,21 @@ __device__ __forceinline__ void run_passes_dir(cx<T>* buf, cx<T>* scratch, const
                                                const cx<T>* __restrict__ tables) {
   for (int ps = 0; ps < f.npass; ps++) {
     const int R = f.radix[ps];
-    const int L = f.p[ps];
+    const FastDiv dNb = f.dNb[ps], dLr = f.dLr[ps];
     const cx<T>* tw = tables + f.tw_off[ps];
     switch (R) {
-      case 2: dif_pass<T, 2, INV>(buf, lay, f.M, ncol, L, tw); break;
-      case 3: dif_pass<T, 3, INV>(buf, lay, f.M, ncol, L, tw); break;
-      case 4: dif_pass<T, 4, INV>(buf, lay, f.M, ncol, L, tw); break;
-      case 5: dif_pass<T, 5, INV>(buf, lay, f.M, ncol, L, tw); break;
-      case 7: dif_pass<T, 7, INV>(buf, lay, f.M, ncol, L, tw); break;
-      case 8: dif_pass<T, 8, INV>(buf, lay, f.M, ncol, L, tw); break;
-      case 16: dif_pass<T, 16, INV>(buf, lay, f.M, ncol, L, tw); break;
+      case 2: dif_pass<T, 2, INV>(buf, lay, f.M, ncol, dNb, dLr, tw); break;
+      case 3: dif_pass<T, 3, INV>(buf, lay, f.M, ncol, dNb, dLr, tw); break;
+      case 4: dif_pass<T, 4, INV>(buf, lay, f.M, ncol, dNb, dLr, tw); break;
+      case 5: dif_pass<T, 5, INV>(buf, lay, f.M, ncol, dNb, dLr, tw); break;
+      case 7: dif_pass<T, 7, INV>(buf, lay, f.M, ncol, dNb, dLr, tw); break;
+      case 8: dif_pass<T, 8, INV>(buf, lay, f.M, ncol, dNb, dLr, tw); break;
+      case 16: dif_pass<T, 16, INV>(buf, lay, f.M, ncol, dNb, dLr, tw); break;
       case 32:
-        if constexpr (EMAX >= 32) { dif_pass<T, 32, INV>(buf, lay, f.M, ncol, L, tw); break; }
+        if constexpr (EMAX >= 32) { dif_pass<T, 32, INV>(buf, lay, f.M, ncol, dNb, dLr, tw); break; }
         // fall through to the direct DFT when 32 complex values exceed the register budget
       default:
-        dif_pass_generic<T, INV>(buf, scratch, lay, f.M, ncol, R, L, tw, tables + f.gen_off[ps]);
+        dif_pass_generic<T, INV>(buf, scratch, lay, f.dM, ncol, R, f.dL[ps], dLr, tw, tables + f.gen_off[ps]);
         break;
     }
   }
@@ -451,17 +462,18 @@ inline __device__ bool kind_needs_pre(int kind) {
 
 // In-place pre-processing of a whole tile: rows 0..n-1 (source) -> 0..M-1.
 template <typename T, int EMAX, class LAY>
-__device__ __forceinline__ void pre_tile(cx<T>* buf, const LAY lay, int kind, int n, int M, int ncol,
+__device__ __forceinline__ void pre_tile(cx<T>* buf, const LAY lay, int kind, int n, const FastDiv dM, int ncol,
                                          const cx<T>* __restrict__ mk) {
   if (!kind_needs_pre(kind)) return;
   cx<T> v[EMAX];
+  const int M = (int)dM.d;
   const int total = M * ncol;
 #pragma unroll
   for (int j = 0; j < EMAX; j++) {
     const int e = threadIdx.x + j * kThreads;
     if (e < total) {
       int m, c;
-      lay.split(e, M, m, c);
+      lay.split(e, dM, m, c);
       v[j] = pre_value<T>(buf, lay, kind, n, M, m, c, mk);
     }
   }
@@ -471,7 +483,7 @@ __device__ __forceinline__ void pre_tile(cx<T>* buf, const LAY lay, int kind, in
     const int e = threadIdx.x + j * kThreads;
     if (e < total) {
       int m, c;
-      lay.split(e, M, m, c);
+      lay.split(e, dM, m, c);
       buf[lay.idx(m, c)] = v[j];
     }
   }
@@ -501,7 +513,7 @@ __device__ __forceinline__ void bluestein_fft(const cx<T>* src, const LS ls, cx<
   const int total = L * ncol;
   for (int e = threadIdx.x; e < total; e += kThreads) {
     int j, c;
-    ld.split(e, L, j, c);
+    ld.split(e, ax.fft.dM, j, c);
     cx<T> v = czero<T>();
     if (j < M) {
       v = pre_value<T>(src, ls, kind, n, M, j, c, mk);
@@ -514,7 +526,7 @@ __device__ __forceinline__ void bluestein_fft(const cx<T>* src, const LS ls, cx<
   run_passes_dir<T, false, EMAX>(dst, dst, ld, ax.fft, ncol, tables);
   for (int e = threadIdx.x; e < total; e += kThreads) {
     int p, c;
-    ld.split(e, L, p, c);
+    ld.split(e, ax.fft.dM, p, c);
     dst[ld.idx(p, c)] = cmul<T>(dst[ld.idx(p, c)], bhat[p]);
   }
   __syncthreads();
@@ -522,7 +534,7 @@ __device__ __forceinline__ void bluestein_fft(const cx<T>* src, const LS ls, cx<
   const int tm = M * ncol;
   for (int e = threadIdx.x; e < tm; e += kThreads) {
     int k, c;
-    ld.split(e, M, k, c);
+    ld.split(e, ax.dblu_M, k, c);
     cx<T> x = cmulc<T>(dst[ld.idx(k, c)], chirp[k]);
     dst[ld.idx(k, c)] = inv ? cconj<T>(x) : x;
   }

@@ -38,6 +38,30 @@ inline __host__ __device__ bool kind_uses_inverse_fft(int k) {
 constexpr int kMaxPass = 12;
 constexpr int kThreads = 256;          // threads per CTA of every sweep kernel
 
+// Unsigned 32-bit division by a run-time invariant d >= 1 as one multiply-high,
+// a subtract, an add and two shifts (Granlund & Montgomery, "Division by
+// invariant integers using multiplication", 1994, Fig. 4.1): with
+// l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (t + ((n - t) >> min(l,1))) >> max(l-1,0), t = mulhi(m, n),
+// exact for every 32-bit n.  The sweep kernels use it for the tile index
+// splits that a hardware-less integer division would otherwise dominate.
+struct FastDiv {
+  uint32_t d, m;
+  int s1, s2;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  int l = 0;
+  while ((1ull << l) < d) l++;
+  const uint64_t m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;  // < 2^32 because 2^l < 2d
+  return FastDiv{d, (uint32_t)m, l < 1 ? l : 1, l > 1 ? l - 1 : 0};
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+  const uint32_t t = __umulhi(n, f.m);
+  return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+#endif
+
 struct FftDesc {
   int M;                  // FFT length
   int npass;
@@ -45,6 +69,10 @@ struct FftDesc {
   int p[kMaxPass];        // block length L of the pass (M / product of the earlier radices)
   int tw_off[kMaxPass];   // offset (complex entries) of the pass twiddles exp(-2 pi i j s/L)
   int gen_off[kMaxPass];  // offset of the radix-R unit roots for generic radices, -1 otherwise
+  FastDiv dM;             // divisions by M and, per pass, by M/R (butterflies per line),
+  FastDiv dNb[kMaxPass];  // L/R (butterfly offset) and L
+  FastDiv dLr[kMaxPass];
+  FastDiv dL[kMaxPass];
 };
 
 struct AxisDesc {
@@ -56,6 +84,7 @@ struct AxisDesc {
   // prime factor: a circular convolution of power-of-two length L >= 2M-1.
   int blu;                // 1: use it (fft describes the length-L passes then)
   int blu_M;              // the DFT length M
+  FastDiv dblu_M;
   int chirp_off;          // c_m = exp(+i pi m^2 / M), m < M
   int bhat_off;           // DFT_L of the chirp kernel / L, in DIF output order
 };
@@ -78,6 +107,7 @@ struct XArgs {
   void* ws;
   int* err;
   int ny;                 // rows per z plane (row r = y + ny*z)
+  FastDiv dnx, dnh, dny;  // divisions by nx, nx/2+1 and ny
   long long g_sy, g_sz;   // element strides of g between y rows and z planes
   long long phi_sy, phi_sz;
 };
@@ -122,6 +152,7 @@ struct PairDivideArgs {
   void* data;             // workspace [nz][ny][pitch] complex
   long long pitch;
   int ncols, nx, ny, nz;
+  FastDiv dncols;
   int per_y, per_z;       // axis is periodic (mirror index (n - k) mod n)
   const void* lam_x;      // kx = 0..nx-1
   const void* lam_y;

@@ -174,7 +174,9 @@ int build_axis(AxisPlan& ax, int bc, int n, double L, int approx, int emax, bool
   }
   d.blu = blu ? 1 : 0;
   d.blu_M = M;
+  d.dblu_M = make_fastdiv((uint32_t)M);
   d.fft.M = Mfft;
+  d.fft.dM = make_fastdiv((uint32_t)Mfft);
   if ((int)radices.size() > kMaxPass) return POISFFT_ERR_UNSUPPORTED_SIZE;
   d.fft.npass = (int)radices.size();
   ax.tab_re.clear();
@@ -191,6 +193,9 @@ int build_axis(AxisPlan& ax, int bc, int n, double L, int approx, int emax, bool
     d.fft.p[i] = Lb;
     d.fft.tw_off[i] = (int)ax.tab_re.size();
     const int Lr = Lb / R;
+    d.fft.dNb[i] = make_fastdiv((uint32_t)(Mfft / R));
+    d.fft.dLr[i] = make_fastdiv((uint32_t)Lr);
+    d.fft.dL[i] = make_fastdiv((uint32_t)Lb);
     for (int s = 1; s < R; s++)
       for (int j = 0; j < Lr; j++) {
         double sn, c;
@@ -427,12 +432,15 @@ int upload_tables(poisfft_plan* p) {
 
 // smem rows of one x line: the in-place line (plus a direct-DFT scratch
 // line), or the source line plus the Bluestein convolution buffer
-int x_line_ld(const poisfft_plan* p) { return p->axes[0].d.blu ? p->nx : p->axes[0].d.fft.M; }
+// (rows are padded by one complex value per 16 (FP32) or 8 (FP64), the
+// kernels' RowTile layout)
+int x_padded(const poisfft_plan* p, int len) { return len + (len >> (p->esize == 4 ? 4 : 3)); }
+int x_line_ld(const poisfft_plan* p) { return x_padded(p, p->axes[0].d.blu ? p->nx : p->axes[0].d.fft.M); }
 size_t x_per_line(const poisfft_plan* p) {
   const AxisPlan& ax = p->axes[0];
   const size_t cx = 2 * p->esize;
-  if (ax.d.blu) return (size_t)(p->nx + ax.d.fft.M) * cx;
-  return (size_t)ax.d.fft.M * cx * (ax.generic ? 2 : 1);
+  if (ax.d.blu) return (size_t)(x_padded(p, p->nx) + x_padded(p, ax.d.fft.M)) * cx;
+  return (size_t)x_padded(p, ax.d.fft.M) * cx * (ax.generic ? 2 : 1);
 }
 // smem bytes per tile column of a strided sweep with `rows_alloc` tile rows
 size_t strided_per_col(const poisfft_plan* p, int axis, int rows_alloc) {
@@ -470,6 +478,10 @@ int plan_x_sweep(poisfft_plan* p, int mode, SweepLaunch& L) {
   a.ws_ld = p->r2c ? p->pitch : 2LL * p->pitch;
   a.ws = p->ws;
   a.err = p->err;
+  a.ny = p->ny;
+  a.dnx = make_fastdiv((uint32_t)p->nx);
+  a.dnh = make_fastdiv((uint32_t)(p->nx / 2 + 1));
+  a.dny = make_fastdiv((uint32_t)p->ny);
   L.grid = (unsigned)((pairs + lines - 1) / lines);
   L.smem = (size_t)lines * per_line;
   const long long field = nrows * p->nx * (long long)p->esize;
@@ -866,6 +878,8 @@ int poisfft_plan_create(poisfft_plan** out, int dims, const int64_t n[], const d
     PairDivideArgs& d = Ls.pda;
     d.pitch = p->pitch;
     d.ncols = p->ncols;
+    d.dncols = make_fastdiv((uint32_t)p->ncols);
+    if ((long long)p->ncols * p->ny > 0x7fffffffLL) { free_plan(p); return POISFFT_ERR_UNSUPPORTED_SIZE; }
     d.nx = p->nx;
     d.ny = p->ny;
     d.nz = p->nz;

@@ -34,7 +34,9 @@ __global__ void __launch_bounds__(kThreads, 2) x_sweep_kernel(const XArgs a) {
   constexpr int EMAX = Emax<T>::value;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
-  const RowTile lay{a.ld};
+  // padding shift of the row tiles: 16 float or 8 double complex values per bank sweep
+  constexpr int PSH = sizeof(T) == 4 ? 4 : 3;
+  const RowTile lay{a.ld, PSH};
   cx<T>* scratch = buf + (size_t)a.lines * a.ld;  // direct-DFT scratch or the Bluestein buffer
   const cx<T>* tables = reinterpret_cast<const cx<T>*>(a.tables);
   const cx<T>* mk = a.ax.mk_off >= 0 ? tables + a.ax.mk_off : nullptr;
@@ -43,6 +45,15 @@ __global__ void __launch_bounds__(kThreads, 2) x_sweep_kernel(const XArgs a) {
   const int M = a.ax.fft.M;
   const long long row0 = (long long)blockIdx.x * 2 * a.lines;
   const int kind = a.mode == 0 ? a.ax.kfwd : a.ax.kinv;
+  // field row r = y + ny*z of the CTA's first line; later rows by one 32-bit
+  // fast division of (y0 + offset) by ny
+  const long long z0 = row0 / a.ny;
+  const int y0 = (int)(row0 - z0 * a.ny);
+  auto field_offset = [&](int dr, long long sy, long long sz) {
+    const uint32_t yy = (uint32_t)(y0 + dr);
+    const uint32_t dz = fdiv(yy, a.dny);
+    return (long long)(yy - dz * (uint32_t)a.ny) * sy + (z0 + dz) * sz;
+  };
 
   // ---- stage A: bring the source lines into smem
   if (a.mode == 0 || !a.r2c) {
@@ -50,12 +61,12 @@ __global__ void __launch_bounds__(kThreads, 2) x_sweep_kernel(const XArgs a) {
     const T* src = reinterpret_cast<const T*>(a.mode == 0 ? a.g : a.ws);
     const int total = a.lines * nx;
     for (int e = threadIdx.x; e < total; e += kThreads) {
-      const int l = e / nx;
+      const int l = (int)fdiv((uint32_t)e, a.dnx);
       const int j = e - l * nx;
       const long long ra = row0 + 2 * l, rb = ra + 1;
       // g rows may sit inside a larger array (strides g_sy, g_sz)
-      const long long oa = a.mode == 0 ? (ra % a.ny) * a.g_sy + (ra / a.ny) * a.g_sz : ra * a.ws_ld;
-      const long long ob = a.mode == 0 ? (rb % a.ny) * a.g_sy + (rb / a.ny) * a.g_sz : rb * a.ws_ld;
+      const long long oa = a.mode == 0 ? field_offset(2 * l, a.g_sy, a.g_sz) : ra * a.ws_ld;
+      const long long ob = a.mode == 0 ? field_offset(2 * l + 1, a.g_sy, a.g_sz) : rb * a.ws_ld;
       const T va = ra < a.nrows ? src[oa + j] : T(0);
       const T vb = rb < a.nrows ? src[ob + j] : T(0);
       buf[lay.idx(j, l)] = mkc<T>(va, vb);
@@ -66,7 +77,7 @@ __global__ void __launch_bounds__(kThreads, 2) x_sweep_kernel(const XArgs a) {
     const int nh = nx / 2 + 1;
     const int total = a.lines * nh;
     for (int e = threadIdx.x; e < total; e += kThreads) {
-      const int l = e / nh;
+      const int l = (int)fdiv((uint32_t)e, a.dnh);
       const int k = e - l * nh;
       const long long ra = row0 + 2 * l, rb = ra + 1;
       const cx<T> A = ra < a.nrows ? src[ra * a.ws_ld + k] : czero<T>();
@@ -86,11 +97,11 @@ __global__ void __launch_bounds__(kThreads, 2) x_sweep_kernel(const XArgs a) {
   cx<T>* res = buf;
   RowTile lres = lay;
   if (a.ax.blu) {
-    lres = RowTile{M};
+    lres = RowTile{M + (M >> PSH), PSH};
     bluestein_fft<T, EMAX>(buf, lay, scratch, lres, a.ax, kind, nx, a.lines, tables, mk);
     res = scratch;
   } else {
-    pre_tile<T, EMAX>(buf, lay, kind, nx, M, a.lines, mk);
+    pre_tile<T, EMAX>(buf, lay, kind, nx, a.ax.fft.dM, a.lines, mk);
     run_passes<T, EMAX>(buf, scratch, lay, a.ax.fft, a.lines, tables, kind_uses_inverse_fft(kind));
   }
 
@@ -100,7 +111,7 @@ __global__ void __launch_bounds__(kThreads, 2) x_sweep_kernel(const XArgs a) {
     const int nh = nx / 2 + 1;
     const int total = a.lines * nh;
     for (int e = threadIdx.x; e < total; e += kThreads) {
-      const int l = e / nh;
+      const int l = (int)fdiv((uint32_t)e, a.dnh);
       const int k = e - l * nh;
       const long long ra = row0 + 2 * l, rb = ra + 1;
       const cx<T> z1 = res[lres.idx(perm[k], l)];
@@ -115,11 +126,11 @@ __global__ void __launch_bounds__(kThreads, 2) x_sweep_kernel(const XArgs a) {
     T* dst = reinterpret_cast<T*>(a.mode == 0 ? a.ws : a.phi);
     const int total = a.lines * nx;
     for (int e = threadIdx.x; e < total; e += kThreads) {
-      const int l = e / nx;
+      const int l = (int)fdiv((uint32_t)e, a.dnx);
       const int k = e - l * nx;
       const long long ra = row0 + 2 * l, rb = ra + 1;
-      const long long oa = a.mode == 0 ? ra * a.ws_ld : (ra % a.ny) * a.phi_sy + (ra / a.ny) * a.phi_sz;
-      const long long ob = a.mode == 0 ? rb * a.ws_ld : (rb % a.ny) * a.phi_sy + (rb / a.ny) * a.phi_sz;
+      const long long oa = a.mode == 0 ? ra * a.ws_ld : field_offset(2 * l, a.phi_sy, a.phi_sz);
+      const long long ob = a.mode == 0 ? rb * a.ws_ld : field_offset(2 * l + 1, a.phi_sy, a.phi_sz);
       const cx<T> v = post_value<T>(res, lres, kind, nx, k, l, mk, perm);
       if (ra < a.nrows) dst[oa + k] = v.x;
       if (rb < a.nrows) dst[ob + k] = v.y;
@@ -161,7 +172,6 @@ __global__ void __launch_bounds__(kThreads, 2) strided_sweep_kernel(const __grid
   const cx<T>* mk = a.ax.mk_off >= 0 ? tables + a.ax.mk_off : nullptr;
   const int* perm = a.perm;
   const int n = a.ax.n;
-  const int M = a.ax.fft.M;
   const int tcol = blockIdx.x % a.ntile_c;
   const int outer = blockIdx.x / a.ntile_c;
   const int c0 = tcol * a.w;
@@ -199,7 +209,7 @@ __global__ void __launch_bounds__(kThreads, 2) strided_sweep_kernel(const __grid
       bluestein_fft<T, EMAX>(buf, lay, scratch, lay, a.ax, kind, n, a.w, tables, mk);
       res = scratch;
     } else {
-      pre_tile<T, EMAX>(buf, lay, kind, n, M, a.w, mk);
+      pre_tile<T, EMAX>(buf, lay, kind, n, a.ax.fft.dM, a.w, mk);
       run_passes<T, EMAX>(buf, scratch, lay, a.ax.fft, a.w, tables, kind_uses_inverse_fft(kind));
     }
     const int total = n * a.w;
@@ -245,7 +255,7 @@ __global__ void __launch_bounds__(kThreads, 2) strided_sweep_kernel(const __grid
   }
 
   // ---- fused: forward, divide by the eigenvalues, backward
-  pre_tile<T, EMAX>(buf, lay, a.ax.kfwd, n, M, a.w, mk);
+  pre_tile<T, EMAX>(buf, lay, a.ax.kfwd, n, a.ax.fft.dM, a.w, mk);
   run_passes<T, EMAX>(buf, scratch, lay, a.ax.fft, a.w, tables, kind_uses_inverse_fft(a.ax.kfwd));
   {
     const T* lin = reinterpret_cast<const T*>(a.lam_in);
@@ -280,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, 2) strided_sweep_kernel(const __grid
     }
     __syncthreads();
   }
-  pre_tile<T, EMAX>(buf, lay, a.ax.kinv, n, M, a.w, mk);
+  pre_tile<T, EMAX>(buf, lay, a.ax.kinv, n, a.ax.fft.dM, a.w, mk);
   run_passes<T, EMAX>(buf, scratch, lay, a.ax.fft, a.w, tables, kind_uses_inverse_fft(a.ax.kinv));
   const int total = n * a.w;
   for (int e = threadIdx.x; e < total; e += kThreads) {
@@ -295,33 +305,33 @@ __global__ void __launch_bounds__(kThreads, 2) strided_sweep_kernel(const __grid
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) pair_divide_kernel(const PairDivideArgs a) {
-  const long long total = (long long)a.ncols * a.ny * a.nz;
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= total) return;
-  const int c = (int)(e % a.ncols);
-  const long long r = e / a.ncols;
-  const int y = (int)(r % a.ny);
-  const int z = (int)(r / a.ny);
-  const int yn = a.per_y ? (a.ny - y) % a.ny : y;
-  const int zn = a.per_z ? (a.nz - z) % a.nz : z;
-  if (z > zn || (z == zn && y > yn)) return;  // the mirror element's thread does the pair
-  cx<T>* ws = reinterpret_cast<cx<T>*>(a.data);
-  const long long i1 = ((long long)z * a.ny + y) * a.pitch + c;
-  const long long i2 = ((long long)zn * a.ny + yn) * a.pitch + c;
-  const cx<T> z1 = ws[i1];
-  const cx<T> z2 = ws[i2];
-  // A(k) = (Z1 + conj Z2)/2, B(k) = (Z1 - conj Z2)/(2i)
-  const cx<T> A = mkc<T>(T(0.5) * (z1.x + z2.x), T(0.5) * (z1.y - z2.y));
-  const cx<T> B = mkc<T>(T(0.5) * (z1.y + z2.y), T(0.5) * (z2.x - z1.x));
-  const T* lx = reinterpret_cast<const T*>(a.lam_x);
-  const T lyz = reinterpret_cast<const T*>(a.lam_y)[y] + reinterpret_cast<const T*>(a.lam_z)[z];
-  const int kxa = 2 * c, kxb = 2 * c + 1;
-  T fa = T(0), fb = T(0);
-  if (kxa < a.nx && !(a.singular && kxa == 0 && y == 0 && z == 0)) fa = T(a.scale) / (lx[kxa] + lyz);
-  if (kxb < a.nx) fb = T(a.scale) / (lx[kxb] + lyz);
-  // Z'(k) = fa A + i fb B; at the mirror A and B are conjugated (Hermitian)
-  ws[i1] = mkc<T>(fa * A.x - fb * B.y, fa * A.y + fb * B.x);
-  if (i2 != i1) ws[i2] = mkc<T>(fa * A.x + fb * B.y, fb * B.x - fa * A.y);
+  // grid.x covers one (c, y) plane, grid.y strides over z
+  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (uint32_t)a.ncols * (uint32_t)a.ny) return;
+  const int y = (int)fdiv(e, a.dncols);
+  const int c = (int)(e - (uint32_t)y * (uint32_t)a.ncols);
+  const int yn = a.per_y ? (y == 0 ? 0 : a.ny - y) : y;
+  for (int z = blockIdx.y; z < a.nz; z += gridDim.y) {
+    const int zn = a.per_z ? (z == 0 ? 0 : a.nz - z) : z;
+    if (z > zn || (z == zn && y > yn)) continue;  // the mirror element's thread does the pair
+    cx<T>* ws = reinterpret_cast<cx<T>*>(a.data);
+    const long long i1 = ((long long)z * a.ny + y) * a.pitch + c;
+    const long long i2 = ((long long)zn * a.ny + yn) * a.pitch + c;
+    const cx<T> z1 = ws[i1];
+    const cx<T> z2 = ws[i2];
+    // A(k) = (Z1 + conj Z2)/2, B(k) = (Z1 - conj Z2)/(2i)
+    const cx<T> A = mkc<T>(T(0.5) * (z1.x + z2.x), T(0.5) * (z1.y - z2.y));
+    const cx<T> B = mkc<T>(T(0.5) * (z1.y + z2.y), T(0.5) * (z2.x - z1.x));
+    const T* lx = reinterpret_cast<const T*>(a.lam_x);
+    const T lyz = reinterpret_cast<const T*>(a.lam_y)[y] + reinterpret_cast<const T*>(a.lam_z)[z];
+    const int kxa = 2 * c, kxb = 2 * c + 1;
+    T fa = T(0), fb = T(0);
+    if (kxa < a.nx && !(a.singular && kxa == 0 && y == 0 && z == 0)) fa = T(a.scale) / (lx[kxa] + lyz);
+    if (kxb < a.nx) fb = T(a.scale) / (lx[kxb] + lyz);
+    // Z'(k) = fa A + i fb B; at the mirror A and B are conjugated (Hermitian)
+    ws[i1] = mkc<T>(fa * A.x - fb * B.y, fa * A.y + fb * B.x);
+    if (i2 != i1) ws[i2] = mkc<T>(fa * A.x + fb * B.y, fb * B.x - fa * A.y);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -348,9 +358,9 @@ cudaError_t launch_strided_sweep(const CUtensorMap& map, const StridedArgs& a, u
 
 template <typename T>
 cudaError_t launch_pair_divide(const PairDivideArgs& a, cudaStream_t s) {
-  const long long total = (long long)a.ncols * a.ny * a.nz;
-  const unsigned grid = (unsigned)((total + 255) / 256);
-  pair_divide_kernel<T><<<grid, 256, 0, s>>>(a);
+  const unsigned gx = (unsigned)(((long long)a.ncols * a.ny + 255) / 256);
+  const unsigned gz = (unsigned)(a.nz < 65535 ? a.nz : 65535);
+  pair_divide_kernel<T><<<dim3(gx, gz), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
