@@ -327,7 +327,9 @@ __device__ __noinline__ void dit_pass(cx<T>* __restrict__ buf, const LAY lay, in
   __syncthreads();
 }
 
-// DIT passes of a power-of-two plan (used by the Bluestein convolution).
+// DIT passes of a plan whose radices are all unrolled (the Bluestein
+// convolution and the fused divide of the strided sweep): digit-reversed
+// input, natural-order output.
 template <typename T, bool INV, int EMAX, class LAY>
 __device__ __forceinline__ void run_passes_dit(cx<T>* buf, const LAY lay, const FftDesc& f, int ncol,
                                                const cx<T>* __restrict__ tables) {
@@ -337,7 +339,10 @@ __device__ __forceinline__ void run_passes_dit(cx<T>* buf, const LAY lay, const 
     const cx<T>* tw = tables + f.tw_off[ps];
     switch (R) {
       case 2: dit_pass<T, 2, INV>(buf, lay, f.M, ncol, dNb, dLr, tw); break;
+      case 3: dit_pass<T, 3, INV>(buf, lay, f.M, ncol, dNb, dLr, tw); break;
       case 4: dit_pass<T, 4, INV>(buf, lay, f.M, ncol, dNb, dLr, tw); break;
+      case 5: dit_pass<T, 5, INV>(buf, lay, f.M, ncol, dNb, dLr, tw); break;
+      case 7: dit_pass<T, 7, INV>(buf, lay, f.M, ncol, dNb, dLr, tw); break;
       case 8: dit_pass<T, 8, INV>(buf, lay, f.M, ncol, dNb, dLr, tw); break;
       case 16: dit_pass<T, 16, INV>(buf, lay, f.M, ncol, dNb, dLr, tw); break;
       default:
@@ -427,32 +432,52 @@ __device__ __forceinline__ cx<T> pre_value(const cx<T>* buf, const LAY& lay, int
 }
 
 // Output k of the transform `kind` from the FFT output held in `buf`; FFT
-// output index i sits at position perm[i] (digit reversal of the passes).
-template <typename T, class LAY>
+// output index i sits at position perm[i] (digit reversal of the DIF
+// passes), or at i itself when NAT (after DIT passes).
+template <typename T, bool NAT = false, class LAY>
 __device__ __forceinline__ cx<T> post_value(const cx<T>* buf, const LAY& lay, int kind, int n, int k, int c,
-                                            const cx<T>* __restrict__ mk, const int* __restrict__ perm) {
+                                            const cx<T>* __restrict__ mk, const int* __restrict__ perm_tab) {
+  auto perm = [&](int i) { return NAT ? i : perm_tab[i]; };
   switch (kind) {
     case TK_DCT2:
     case TK_DST2: {
       // X_k = w_k Y_k + conj(w_k) Y_{(n-k) mod n};  DST-II reads DCT-II output n-1-k
       const int kk = (kind == TK_DCT2) ? k : n - 1 - k;
       const cx<T> w = mk[kk];
-      const cx<T> y1 = buf[lay.idx(perm[kk], c)];
-      const cx<T> y2 = buf[lay.idx(perm[kk == 0 ? 0 : n - kk], c)];
+      const cx<T> y1 = buf[lay.idx(perm(kk), c)];
+      const cx<T> y2 = buf[lay.idx(perm(kk == 0 ? 0 : n - kk), c)];
       return cadd<T>(cmul<T>(w, y1), cmulc<T>(y2, w));
     }
     case TK_DST1:
-      return mul_i<T>(buf[lay.idx(perm[k + 1], c)]);
+      return mul_i<T>(buf[lay.idx(perm(k + 1), c)]);
     case TK_DCT3:
     case TK_DST3: {
       // outputs 2j and 2j+1 are FFT outputs j and n-1-j
       const int pos = (k & 1) ? n - 1 - (k >> 1) : (k >> 1);
-      cx<T> v = buf[lay.idx(perm[pos], c)];
+      cx<T> v = buf[lay.idx(perm(pos), c)];
       if (kind == TK_DST3 && (k & 1)) v = mkc<T>(-v.x, -v.y);
       return v;
     }
     default:  // DFT, IDFT, DCT1, NULL
-      return buf[lay.idx(perm[k], c)];
+      return buf[lay.idx(perm(k), c)];
+  }
+}
+
+// Calls f(KindC<kind>{}) so that the transform kind is a compile-time
+// constant inside the element loops (no per-element indirect branch).
+template <int K> struct KindC { static constexpr int value = K; };
+template <class F>
+__device__ __forceinline__ void with_kind(int kind, F&& f) {
+  switch (kind) {
+    case TK_DFT: f(KindC<TK_DFT>{}); break;
+    case TK_IDFT: f(KindC<TK_IDFT>{}); break;
+    case TK_DCT2: f(KindC<TK_DCT2>{}); break;
+    case TK_DCT3: f(KindC<TK_DCT3>{}); break;
+    case TK_DST2: f(KindC<TK_DST2>{}); break;
+    case TK_DST3: f(KindC<TK_DST3>{}); break;
+    case TK_DST1: f(KindC<TK_DST1>{}); break;
+    case TK_DCT1: f(KindC<TK_DCT1>{}); break;
+    default: f(KindC<TK_NULL>{}); break;
   }
 }
 
@@ -465,29 +490,34 @@ template <typename T, int EMAX, class LAY>
 __device__ __forceinline__ void pre_tile(cx<T>* buf, const LAY lay, int kind, int n, const FastDiv dM, int ncol,
                                          const cx<T>* __restrict__ mk) {
   if (!kind_needs_pre(kind)) return;
-  cx<T> v[EMAX];
-  const int M = (int)dM.d;
-  const int total = M * ncol;
+  with_kind(kind, [&](auto kc) {
+    constexpr int K = decltype(kc)::value;
+    if constexpr (K != TK_DFT && K != TK_IDFT && K != TK_NULL) {
+      cx<T> v[EMAX];
+      const int M = (int)dM.d;
+      const int total = M * ncol;
 #pragma unroll
-  for (int j = 0; j < EMAX; j++) {
-    const int e = threadIdx.x + j * kThreads;
-    if (e < total) {
-      int m, c;
-      lay.split(e, dM, m, c);
-      v[j] = pre_value<T>(buf, lay, kind, n, M, m, c, mk);
-    }
-  }
-  __syncthreads();
+      for (int j = 0; j < EMAX; j++) {
+        const int e = threadIdx.x + j * kThreads;
+        if (e < total) {
+          int m, c;
+          lay.split(e, dM, m, c);
+          v[j] = pre_value<T>(buf, lay, K, n, M, m, c, mk);
+        }
+      }
+      __syncthreads();
 #pragma unroll
-  for (int j = 0; j < EMAX; j++) {
-    const int e = threadIdx.x + j * kThreads;
-    if (e < total) {
-      int m, c;
-      lay.split(e, dM, m, c);
-      buf[lay.idx(m, c)] = v[j];
+      for (int j = 0; j < EMAX; j++) {
+        const int e = threadIdx.x + j * kThreads;
+        if (e < total) {
+          int m, c;
+          lay.split(e, dM, m, c);
+          buf[lay.idx(m, c)] = v[j];
+        }
+      }
+      __syncthreads();
     }
-  }
-  __syncthreads();
+  });
 }
 
 // ---------------------------------------------------------------------------

@@ -138,6 +138,7 @@ struct StridedArgs {
   double scale;           // product of the Table 2 normalisations
   int singular;           // every axis P/NR/NS: zero the all-zero mode
   int packed;             // 1: column c carries kx = 2c (real part) and 2c+1 (imag part)
+  int dit_fused;          // mode 2 with unrolled radices only: backward FFT as DIT passes
   int nx;                 // number of x points (valid kx < nx when packed)
   int* err;
 };

@@ -540,6 +540,7 @@ int plan_strided_sweep(poisfft_plan* p, int axis, int mode, SweepLaunch& L) {
   s.scale = sc;
   s.singular = p->singular;
   s.packed = p->r2c ? 0 : 1;
+  s.dit_fused = mode == 2 && !ax.d.blu && !ax.generic && !(s.packed && ax.d.kfwd == TK_DFT);
   s.nx = p->nx;
   s.err = p->err;
   L.grid = (unsigned)((long long)s.ntile_c * s.nouter);

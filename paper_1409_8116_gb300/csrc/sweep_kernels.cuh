@@ -156,6 +156,105 @@ __device__ __forceinline__ T eigen_factor(const StridedArgs& a, const T* lin, co
   return T(a.scale) / den;
 }
 
+// Eigenvalue factors of one workspace column at outer index o: the real
+// part (and, for packed real x columns, the imaginary part separately) of a
+// spectral value at axis index k is multiplied by
+// s / (lam_in[kx] + lam_ax[k] + lam_out[o]), 0 for padding columns and for the
+// zero mode of a singular problem.
+template <typename T>
+struct ColumnDivide {
+  const T* lax;
+  T s, ba, bb;
+  bool oka, okb, za, zb;
+  __device__ __forceinline__ ColumnDivide(const StridedArgs& a, int col, int o) {
+    const T* lin = reinterpret_cast<const T*>(a.lam_in);
+    const T lo = reinterpret_cast<const T*>(a.lam_out)[o];
+    lax = reinterpret_cast<const T*>(a.lam_ax);
+    s = T(a.scale);
+    const int kxa = a.packed ? 2 * col : col;
+    const int kxb = a.packed ? 2 * col + 1 : col;
+    oka = kxa < a.nx;
+    okb = kxb < a.nx;
+    ba = oka ? lin[kxa] + lo : T(1);
+    bb = okb ? lin[kxb] + lo : T(1);
+    za = a.singular && kxa == 0 && o == 0;
+    zb = a.singular && kxb == 0 && o == 0;
+  }
+  __device__ __forceinline__ cx<T> operator()(cx<T> x, int k) const {
+    const T l = lax[k];
+    const T fa = (oka && !(za && k == 0)) ? s / (ba + l) : T(0);
+    const T fb = (okb && !(zb && k == 0)) ? s / (bb + l) : T(0);
+    return mkc<T>(x.x * fa, x.y * fb);
+  }
+};
+
+// Fused middle step of the strided sweep in the digit-reversed layout left by
+// the forward DIF passes: post-processing of the forward transform, the
+// eigenvalue divide and pre-processing of the backward transform, computed
+// in place for the pair of FFT indices that each output depends on, so that
+// the backward FFT runs as DIT passes (digit-reversed input, natural output).
+//   DCT-II -> DCT-III  (n points, pairs m, n-m):
+//     P_j = w_j Y_j + conj(w_j) Y_{n-j}  (the DCT-II value j, w_j = exp(-i pi j/2n)),
+//     V_m = conj(w_m) (d(m) P_m - i d(n-m) P_{n-m}),  d(n) P_n := 0
+//   DST-II -> DST-III: the same with d(j) -> d(n-1-j) (DST-II output k is
+//     DCT-II value n-1-k; DST-III input j is read at n-1-j)
+//   DST-I (M = 2(n+1)): X_k = i Y_{k+1};  V_m = d(m-1) X_{m-1} = -V_{M-m}, V_0 = V_{n+1} = 0
+//   DCT-I (M = 2(n-1)): X_k = Y_k;  V_m = V_{M-m} = d(m) Y_m
+//   DFT / length 1: V_k = d(k) Y_k
+// Ends with a barrier.
+template <typename T, class LAY>
+__device__ __forceinline__ void fused_divide_pairs(cx<T>* buf, const LAY lay, int kfwd, int n, int M, int c, int g0,
+                                                   int G, const ColumnDivide<T>& D, const cx<T>* __restrict__ mk,
+                                                   const int* __restrict__ perm) {
+  switch (kfwd) {
+    case TK_DCT2:
+    case TK_DST2: {
+      const bool ds = kfwd == TK_DST2;
+      for (int m = g0; 2 * m <= n; m += G) {
+        const int mp = m == 0 ? 0 : n - m;
+        const int pm = perm[m], pp = perm[mp];
+        const cx<T> ym = buf[lay.idx(pm, c)];
+        const cx<T> yp = buf[lay.idx(pp, c)];
+        const cx<T> wm = mk[m], wp = mk[mp];
+        const cx<T> Pm = cadd<T>(cmul<T>(wm, ym), cmulc<T>(yp, wm));
+        const cx<T> Pp = cadd<T>(cmul<T>(wp, yp), cmulc<T>(ym, wp));
+        const cx<T> fm = D(Pm, ds ? n - 1 - m : m);
+        const cx<T> fp = m == 0 ? czero<T>() : D(Pp, ds ? m - 1 : n - m);
+        buf[lay.idx(pm, c)] = cmulc<T>(mkc<T>(fm.x + fp.y, fm.y - fp.x), wm);  // conj(w_m)(f_m - i f_{n-m})
+        if (m != 0 && mp != m) buf[lay.idx(pp, c)] = cmulc<T>(mkc<T>(fp.x + fm.y, fp.y - fm.x), wp);
+      }
+      break;
+    }
+    case TK_DST1:
+      for (int m = g0; m <= n + 1; m += G) {
+        if (m == 0 || m == n + 1) {
+          buf[lay.idx(perm[m], c)] = czero<T>();
+          continue;
+        }
+        const int pm = perm[m];
+        const cx<T> f = D(mul_i<T>(buf[lay.idx(pm, c)]), m - 1);
+        buf[lay.idx(pm, c)] = f;
+        buf[lay.idx(perm[M - m], c)] = mkc<T>(-f.x, -f.y);
+      }
+      break;
+    case TK_DCT1:
+      for (int m = g0; m < n; m += G) {
+        const int pm = perm[m];
+        const cx<T> f = D(buf[lay.idx(pm, c)], m);
+        buf[lay.idx(pm, c)] = f;
+        if (m >= 1 && m <= n - 2) buf[lay.idx(perm[M - m], c)] = f;
+      }
+      break;
+    default:
+      for (int k = g0; k < M; k += G) {
+        const int pk = perm[k];
+        buf[lay.idx(pk, c)] = D(buf[lay.idx(pk, c)], k);
+      }
+      break;
+  }
+  __syncthreads();
+}
+
 // Two CTAs per SM: the register cap (128) makes the compiler spill a few
 // kilobytes per thread, but the doubled occupancy more than pays for it
 // (512 uneven batch problems: 153 -> 135 ms of summed solve time).
@@ -212,11 +311,14 @@ __global__ void __launch_bounds__(kThreads, 2) strided_sweep_kernel(const __grid
       pre_tile<T, EMAX>(buf, lay, kind, n, a.ax.fft.dM, a.w, mk);
       run_passes<T, EMAX>(buf, scratch, lay, a.ax.fft, a.w, tables, kind_uses_inverse_fft(kind));
     }
-    const int total = n * a.w;
-    for (int e = threadIdx.x; e < total; e += kThreads) {
-      const int c = e & (a.w - 1);
-      const int k = e >> a.lw;
-      if (c < ncol_valid) out[(size_t)k * a.s_axis + c] = post_value<T>(res, lay, kind, n, k, c, mk, perm);
+    // w divides kThreads: every thread keeps one column
+    const int c = threadIdx.x & (a.w - 1);
+    if (c < ncol_valid) {
+      const int G = kThreads >> a.lw;
+      with_kind(kind, [&](auto kc) {
+        for (int k = threadIdx.x >> a.lw; k < n; k += G)
+          out[(size_t)k * a.s_axis + c] = post_value<T>(res, lay, decltype(kc)::value, n, k, c, mk, perm);
+      });
     }
     return;
   }
@@ -254,7 +356,28 @@ __global__ void __launch_bounds__(kThreads, 2) strided_sweep_kernel(const __grid
     return;
   }
 
-  // ---- fused: forward, divide by the eigenvalues, backward
+  if (a.dit_fused) {
+    // ---- fused: forward (DIF), pairwise divide in place, backward (DIT)
+    pre_tile<T, EMAX>(buf, lay, a.ax.kfwd, n, a.ax.fft.dM, a.w, mk);
+    run_passes<T, EMAX>(buf, scratch, lay, a.ax.fft, a.w, tables, kind_uses_inverse_fft(a.ax.kfwd));
+    const int c = threadIdx.x & (a.w - 1);
+    const int g0 = threadIdx.x >> a.lw, G = kThreads >> a.lw;
+    const ColumnDivide<T> D(a, c0 + c, outer);
+    fused_divide_pairs<T>(buf, lay, a.ax.kfwd, n, a.ax.fft.M, c, g0, G, D, mk, perm);
+    if (kind_uses_inverse_fft(a.ax.kinv))
+      run_passes_dit<T, true, EMAX>(buf, lay, a.ax.fft, a.w, tables);
+    else
+      run_passes_dit<T, false, EMAX>(buf, lay, a.ax.fft, a.w, tables);
+    if (c < ncol_valid) {
+      with_kind(a.ax.kinv, [&](auto kc) {
+        for (int k = g0; k < n; k += G)
+          out[(size_t)k * a.s_axis + c] = post_value<T, true>(buf, lay, decltype(kc)::value, n, k, c, mk, perm);
+      });
+    }
+    return;
+  }
+
+  // ---- fused (plans with a direct-DFT pass): forward, divide by the eigenvalues, backward
   pre_tile<T, EMAX>(buf, lay, a.ax.kfwd, n, a.ax.fft.dM, a.w, mk);
   run_passes<T, EMAX>(buf, scratch, lay, a.ax.fft, a.w, tables, kind_uses_inverse_fft(a.ax.kfwd));
   {
