@@ -252,41 +252,69 @@ __device__ __noinline__ void dif_pass(cx<T>* __restrict__ buf, const LAY lay, in
   __syncthreads();
 }
 
-// Direct DFT butterflies for radices without an unrolled kernel (primes > 7):
-// every output reads its R inputs from `buf` and goes to `scratch`; the tile
-// is copied back afterwards.  O(R) work per point, no per-thread arrays.
+// Direct DFT butterflies for radices without an unrolled kernel (odd primes
+// > 7), in the symmetric form: with p_q = u_q + u_{R-q}, m_q = u_q - u_{R-q}
+// (q = 1..H, H = (R-1)/2), a_s = u_0 + sum_q p_q cos(2 pi q s/R) and
+// b_s = sum_q m_q sin(2 pi q s/R), the outputs are y_s = a_s -+ i b_s and
+// y_{R-s} = a_s +- i b_s, y_0 = u_0 + sum_q p_q.  A work item is one
+// butterfly and one output pair (s, R-s) (group 0: y_0), so each input pair
+// is read once per two outputs.  Results go to `scratch`, and the tile is
+// copied back afterwards.  roots[m] = exp(-2 pi i m/R).
 template <typename T, bool INV, class LAY>
 __device__ __noinline__ void dif_pass_generic(cx<T>* __restrict__ buf, cx<T>* __restrict__ scratch, const LAY lay,
                                               const FastDiv dM, int ncol, int R, const FastDiv dL, const FastDiv dLr,
                                               const cx<T>* __restrict__ tw, const cx<T>* __restrict__ roots) {
   const int Lr = (int)dLr.d;
   const int L = (int)dL.d;
-  const int total = (int)dM.d * ncol;
+  const int M = (int)dM.d;
+  const int H = (R - 1) >> 1;
+  const int items = (M / R) * (H + 1);  // per column
+  const FastDiv dG = make_fastdiv((uint32_t)(H + 1));
+  const FastDiv dI = make_fastdiv((uint32_t)items);
+  const int total = items * ncol;
   for (int e = threadIdx.x; e < total; e += kThreads) {
-    int pos, c;
-    lay.split(e, dM, pos, c);
-    const int blk = (int)fdiv((uint32_t)pos, dL);
-    const int rem = pos - blk * L;
-    const int s = (int)fdiv((uint32_t)rem, dLr);
-    const int j = rem - s * Lr;
+    int it, c;
+    lay.split(e, dI, it, c);
+    const int t = (int)fdiv((uint32_t)it, dG);  // butterfly
+    const int g = it - t * (H + 1);             // output pair
+    const int blk = (int)fdiv((uint32_t)t, dLr);
+    const int j = t - blk * Lr;
     const int base = blk * L + j;
-    cx<T> acc = czero<T>();
-    int qs = 0;  // (q*s) mod R
-    for (int q = 0; q < R; q++) {
-      const cx<T> r = roots[qs];
-      const cx<T> x = buf[lay.idx(base + q * Lr, c)];
-      acc = cadd<T>(acc, INV ? cmulc<T>(x, r) : cmul<T>(x, r));
-      qs += s;
+    const cx<T> u0 = buf[lay.idx(base, c)];
+    if (g == 0) {
+      cx<T> y = u0;
+      for (int q = 1; q < R; q++) y = cadd<T>(y, buf[lay.idx(base + q * Lr, c)]);
+      scratch[lay.idx(base, c)] = y;
+      continue;
+    }
+    cx<T> a = u0, b = czero<T>();
+    int qs = 0;  // (q*g) mod R
+    for (int q = 1; q <= H; q++) {
+      qs += g;
       if (qs >= R) qs -= R;
+      const cx<T> x1 = buf[lay.idx(base + q * Lr, c)];
+      const cx<T> x2 = buf[lay.idx(base + (R - q) * Lr, c)];
+      const cx<T> r = roots[qs];  // (cos, -sin)
+      a.x += r.x * (x1.x + x2.x);
+      a.y += r.x * (x1.y + x2.y);
+      b.x -= r.y * (x1.x - x2.x);
+      b.y -= r.y * (x1.y - x2.y);
     }
-    if (j != 0 && s != 0) {
-      const cx<T> w = tw[(s - 1) * Lr + j];
-      acc = INV ? cmulc<T>(acc, w) : cmul<T>(acc, w);
+    const cx<T> ib = mul_i<T>(b);
+    cx<T> y1 = INV ? cadd<T>(a, ib) : csub<T>(a, ib);  // output g
+    cx<T> y2 = INV ? csub<T>(a, ib) : cadd<T>(a, ib);  // output R - g
+    if (j != 0) {
+      const cx<T> w1 = tw[(g - 1) * Lr + j];
+      const cx<T> w2 = tw[(R - g - 1) * Lr + j];
+      y1 = INV ? cmulc<T>(y1, w1) : cmul<T>(y1, w1);
+      y2 = INV ? cmulc<T>(y2, w2) : cmul<T>(y2, w2);
     }
-    scratch[lay.idx(pos, c)] = acc;
+    scratch[lay.idx(base + g * Lr, c)] = y1;
+    scratch[lay.idx(base + (R - g) * Lr, c)] = y2;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < total; e += kThreads) {
+  const int tot2 = M * ncol;
+  for (int e = threadIdx.x; e < tot2; e += kThreads) {
     int pos, c;
     lay.split(e, dM, pos, c);
     buf[lay.idx(pos, c)] = scratch[lay.idx(pos, c)];

@@ -49,7 +49,7 @@ struct FastDiv {
   uint32_t d, m;
   int s1, s2;
 };
-inline FastDiv make_fastdiv(uint32_t d) {
+inline __host__ __device__ FastDiv make_fastdiv(uint32_t d) {
   int l = 0;
   while ((1ull << l) < d) l++;
   const uint64_t m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;  // < 2^32 because 2^l < 2d

@@ -205,6 +205,7 @@ int build_axis(AxisPlan& ax, int bc, int n, double L, int approx, int emax, bool
     if (is_unrolled_radix(R, emax)) {
       d.fft.gen_off[i] = -1;
     } else {
+      if (R % 2 == 0) return POISFFT_ERR_UNSUPPORTED_SIZE;  // the direct pass takes odd radices only
       ax.generic = true;
       d.fft.gen_off[i] = (int)ax.tab_re.size();
       for (int m = 0; m < R; m++) {

@@ -264,11 +264,11 @@ __device__ __forceinline__ void fused_divide_pairs(cx<T>* buf, const LAY lay, in
   __syncthreads();
 }
 
-// Two CTAs per SM: the register cap (128) makes the compiler spill a few
-// kilobytes per thread, but the doubled occupancy more than pays for it
-// (512 uneven batch problems: 153 -> 135 ms of summed solve time).
+// Three CTAs per SM (80 registers; the staging arrays of the pre-processing
+// spill to L1): 512 uneven batch problems 63.9 -> 60.8 ms against two CTAs
+// per SM with a 128-register cap (which in turn beat one CTA without a cap).
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 2) strided_sweep_kernel(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(kThreads, 3) strided_sweep_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                  const StridedArgs a) {
   constexpr int EMAX = Emax<T>::value;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
