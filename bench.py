@@ -55,7 +55,7 @@ BC_NAME = {0: "P", 1: "DR", 2: "DS", 3: "NR", 4: "NS"}
 # Valid only while the kernel sources hash to TRAFFIC_SRC_SHA256.
 TRAFFIC_RATIO = {("strided_sweep", "fused"): 0.980, ("strided_sweep", "forward"): 0.979,
                  ("strided_sweep", "backward"): 0.984}
-TRAFFIC_SRC_SHA256 = "3c01acd910b7930b792e25b4b247cf333105e094425b540006c9c8931aa14de9"
+TRAFFIC_SRC_SHA256 = "cbf66f9cd05f35aa2f4eb5b148953195a64bc3f90dadbc41fbd60bc92cfde0ed"
 TRAFFIC_SOURCES = ["fast_kernels.cuh", "fft_engine.cuh", "fast_f32.cu"]
 
 
