@@ -172,7 +172,9 @@ int poisfft_plan_autotune(poisfft_plan* plan, void* stream);
 /* ---- Batched solves (many independent problems; no paper counterpart) ----
  * poisfft_batch_create: one plan per problem i with dims[i], n[3i..3i+2],
  *   L[3i..3i+2], bc[6i..6i+5] (entries beyond dims[i] ignored), a shared
- *   approx and dtype; every plan is autotuned (poisfft_plan_autotune).
+ *   approx and dtype; the plans keep their default tile shapes (the
+ *   per-plan autotuner times a problem alone on the GPU, and its narrower
+ *   tiles are slower when the batch's problems run concurrently).
  *   Fails with the first failing plan's status.
  * poisfft_batch_solve: solves every problem (phi[i], g[i] as in
  *   poisfft_solve) on `stream`.  The problems' launches run on forked

@@ -1519,12 +1519,11 @@ int poisfft_batch_create(poisfft_batch** out, int count, const int dims[], const
       free_batch(b);
       return rc;
     }
+    // No per-plan autotuning here: the tuner times each problem alone on an
+    // idle GPU and picks narrower tiles, while inside the batch graph the
+    // problems run concurrently and the default tiles are faster (512
+    // uneven problems: 52.8 against 58.3 ms per step).
     b->plans.push_back(p);
-    const int rt = poisfft_plan_autotune(p, nullptr);
-    if (rt != POISFFT_OK) {
-      free_batch(b);
-      return rt;
-    }
   }
   const int ns = std::min(kBatchStreams, count);
   load.assign(ns, 0.0);
