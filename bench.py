@@ -453,6 +453,9 @@ def run_batch(args):
     gs = [torch.from_numpy(W.normal(tuple(reversed(p["n"])), p["gseed"], dtype=np.float32)).cuda() for p in probs]
     phis = [torch.empty_like(x) for x in gs]
     stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    chosen, tune_ms = batch.autotune(phis, gs, stream)
+    t_tune = time.perf_counter() - t0
     for _ in range(args.warmup):
         batch.solve(phis, gs, stream)
     stream.synchronize()
@@ -510,6 +513,8 @@ def run_batch(args):
                    "l2": "inputs larger than L2 (2.7 GB over the batch)"},
         "plain_ms_per_step": ms_plain / args.steps, "speedup_vs_plain": ms_plain / ms_graph,
         "create_s": t_create, "max_rel_err_vs_fp64_first64": err,
+        "autotune": {"kept": pb.Batch.TUNE_CANDIDATES[chosen],
+                     "ms_per_replay": dict(zip(pb.Batch.TUNE_CANDIDATES, tune_ms)), "seconds": t_tune},
         "roofline": {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None,
                      "kernel": "batch graph (per-launch timing not available inside a graph)",
                      "peak_source": f"{peak_kind} hbm_gbs"},

@@ -172,10 +172,9 @@ int poisfft_plan_autotune(poisfft_plan* plan, void* stream);
 /* ---- Batched solves (many independent problems; no paper counterpart) ----
  * poisfft_batch_create: one plan per problem i with dims[i], n[3i..3i+2],
  *   L[3i..3i+2], bc[6i..6i+5] (entries beyond dims[i] ignored), a shared
- *   approx and dtype; the plans keep their default tile shapes (the
- *   per-plan autotuner times a problem alone on the GPU, and its narrower
- *   tiles are slower when the batch's problems run concurrently).
- *   Fails with the first failing plan's status.
+ *   approx and dtype, with the default tile shapes (poisfft_batch_autotune
+ *   tunes them in the batch's own setting).  Fails with the first failing
+ *   plan's status.
  * poisfft_batch_solve: solves every problem (phi[i], g[i] as in
  *   poisfft_solve) on `stream`.  The problems' launches run on forked
  *   streams inside one CUDA graph, captured on the first call and replayed
@@ -184,6 +183,17 @@ int poisfft_plan_autotune(poisfft_plan* plan, void* stream);
  *   stream (use a created stream).
  * poisfft_batch_solve_sequential: the same problems one after another on
  *   `stream` without a graph (the plain form, for comparison).
+ * poisfft_batch_autotune: tile tuning in the batch's own setting.  Times
+ *   the whole graph (one capture, then 4 replays on `stream`) under each of
+ *   POISFFT_BATCH_TUNE_CANDIDATES configurations of the general-kernel tile
+ *   shapes: 0 = the shapes as created, 1 = every strided tile and x line
+ *   block halved, 2 = every plan tuned alone (poisfft_plan_autotune); keeps
+ *   the fastest.  phi and g as in poisfft_batch_solve (phi is overwritten
+ *   with solutions).  ms (may be NULL) receives the milliseconds per graph
+ *   replay of each candidate, chosen (may be NULL) the kept one.
+ *   Synchronises `stream`; the next poisfft_batch_solve re-captures the
+ *   graph.  Returns POISFFT_OK, INVALID_ARG, ALLOC or CUDA (on failure the
+ *   shapes as created are restored).
  * poisfft_batch_check: poisfft_check over all plans (synchronises).
  * poisfft_batch_destroy: frees the plans, streams and graph. */
 typedef struct poisfft_batch poisfft_batch;
@@ -191,6 +201,9 @@ int poisfft_batch_create(poisfft_batch** out, int count, const int dims[], const
                          const int bc[], int approx, int dtype);
 int poisfft_batch_solve(poisfft_batch* batch, void* const phi[], const void* const g[], void* stream);
 int poisfft_batch_solve_sequential(poisfft_batch* batch, void* const phi[], const void* const g[], void* stream);
+#define POISFFT_BATCH_TUNE_CANDIDATES 3
+int poisfft_batch_autotune(poisfft_batch* batch, void* const phi[], const void* const g[], void* stream,
+                           double ms[POISFFT_BATCH_TUNE_CANDIDATES], int* chosen);
 int poisfft_batch_check(poisfft_batch* batch, void* stream);
 int poisfft_batch_destroy(poisfft_batch* batch);
 

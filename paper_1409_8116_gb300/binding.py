@@ -49,6 +49,7 @@ EXPORTED = [
     "poisfft_batch_create",
     "poisfft_batch_solve",
     "poisfft_batch_solve_sequential",
+    "poisfft_batch_autotune",
     "poisfft_batch_check",
     "poisfft_batch_destroy",
     "poisfft_pcg_create",
@@ -125,6 +126,9 @@ def _load():
     for nm in ("poisfft_batch_solve", "poisfft_batch_solve_sequential"):
         getattr(lib, nm).argtypes = [ctypes.c_void_p, vpp, vpp, ctypes.c_void_p]
         getattr(lib, nm).restype = ctypes.c_int
+    lib.poisfft_batch_autotune.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+    lib.poisfft_batch_autotune.restype = ctypes.c_int
     lib.poisfft_batch_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     lib.poisfft_batch_check.restype = ctypes.c_int
     lib.poisfft_batch_destroy.argtypes = [ctypes.c_void_p]
@@ -383,6 +387,20 @@ class Batch:
         rc = lib.poisfft_batch_solve_sequential(self._b, self._ptrs(phis), self._ptrs(gs), _stream(stream))
         if rc != OK:
             raise PoisFFTError(rc, "poisfft_batch_solve_sequential")
+
+    TUNE_CANDIDATES = ("as created", "tiles halved", "each plan tuned alone")
+
+    def autotune(self, phis, gs, stream=None):
+        """Times the batch graph under each tile configuration and keeps the
+        fastest (phis are overwritten).  Returns (chosen index, ms per replay
+        of every candidate)."""
+        ms = (ctypes.c_double * len(self.TUNE_CANDIDATES))()
+        chosen = ctypes.c_int()
+        rc = lib.poisfft_batch_autotune(self._b, self._ptrs(phis), self._ptrs(gs), _stream(stream), ms,
+                                        ctypes.byref(chosen))
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_batch_autotune")
+        return chosen.value, list(ms)
 
     def check(self, stream=None):
         return lib.poisfft_batch_check(self._b, _stream(stream))

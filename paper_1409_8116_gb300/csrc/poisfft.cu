@@ -1499,6 +1499,29 @@ int batch_record(poisfft_batch* b, void* const phi[], const void* const g[], cud
   return POISFFT_OK;
 }
 
+void batch_drop_graph(poisfft_batch* b) {
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  b->g_cached.clear();
+  b->phi_cached.clear();
+}
+
+int batch_apply(poisfft_batch* b, const std::vector<std::vector<SweepLaunch>>& cfg) {
+  for (size_t i = 0; i < b->plans.size(); i++) {
+    b->plans[i]->sweeps = cfg[i];
+    const int rc = encode_maps(b->plans[i]);
+    if (rc != POISFFT_OK) return rc;
+  }
+  batch_drop_graph(b);
+  return POISFFT_OK;
+}
+
+std::vector<std::vector<SweepLaunch>> batch_snapshot(const poisfft_batch* b) {
+  std::vector<std::vector<SweepLaunch>> cfg(b->plans.size());
+  for (size_t i = 0; i < b->plans.size(); i++) cfg[i] = b->plans[i]->sweeps;
+  return cfg;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1521,8 +1544,7 @@ int poisfft_batch_create(poisfft_batch** out, int count, const int dims[], const
     }
     // No per-plan autotuning here: the tuner times each problem alone on an
     // idle GPU and picks narrower tiles, while inside the batch graph the
-    // problems run concurrently and the default tiles are faster (512
-    // uneven problems: 52.8 against 58.3 ms per step).
+    // problems run concurrently (poisfft_batch_autotune times the graph).
     b->plans.push_back(p);
   }
   const int ns = std::min(kBatchStreams, count);
@@ -1585,6 +1607,65 @@ int poisfft_batch_solve(poisfft_batch* b, void* const phi[], const void* const g
     b->stream_cached = st;
   }
   return cudaGraphLaunch(b->exec, st) == cudaSuccess ? POISFFT_OK : POISFFT_ERR_CUDA;
+}
+
+int poisfft_batch_autotune(poisfft_batch* b, void* const phi[], const void* const g[], void* stream,
+                           double ms[POISFFT_BATCH_TUNE_CANDIDATES], int* chosen) {
+  if (!b || !phi || !g) return POISFFT_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // candidate 0: the shapes as created
+  std::vector<std::vector<SweepLaunch>> cfg[POISFFT_BATCH_TUNE_CANDIDATES];
+  cfg[0] = batch_snapshot(b);
+  // candidate 1: general tiles halved (more, smaller CTAs)
+  for (size_t i = 0; i < b->plans.size(); i++) {
+    poisfft_plan* p = b->plans[i];
+    const int wmin = p->esize == 4 ? 2 : 1;
+    for (SweepLaunch& L : p->sweeps) {
+      if (L.kind == 1 && L.sa.w / 2 >= wmin) set_strided_width(p, L, L.sa.w / 2);
+      else if (L.kind == 0 && L.xa.lines / 2 >= 1) set_x_lines(p, L, L.xa.lines / 2);
+    }
+  }
+  cfg[1] = batch_snapshot(b);
+  // candidate 2: every plan tuned alone on the GPU
+  int rc = batch_apply(b, cfg[0]);
+  for (size_t i = 0; rc == POISFFT_OK && i < b->plans.size(); i++) rc = poisfft_plan_autotune(b->plans[i], stream);
+  if (rc != POISFFT_OK) return rc;
+  cfg[2] = batch_snapshot(b);
+
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return POISFFT_ERR_CUDA;
+  }
+  constexpr int kReps = 4;
+  double t[POISFFT_BATCH_TUNE_CANDIDATES];
+  int best = 0;
+  for (int c = 0; c < POISFFT_BATCH_TUNE_CANDIDATES && rc == POISFFT_OK; c++) {
+    rc = batch_apply(b, cfg[c]);
+    if (rc == POISFFT_OK) rc = poisfft_batch_solve(b, phi, g, stream);  // capture and warm up
+    if (rc != POISFFT_OK) break;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < kReps && rc == POISFFT_OK; r++) rc = poisfft_batch_solve(b, phi, g, stream);
+    cudaEventRecord(e1, st);
+    float f = 0.f;
+    if (rc == POISFFT_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&f, e0, e1) != cudaSuccess))
+      rc = POISFFT_ERR_CUDA;
+    t[c] = f / kReps;
+    if (rc == POISFFT_OK && t[c] < t[best]) best = c;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != POISFFT_OK) {
+    cudaGetLastError();
+    batch_apply(b, cfg[0]);
+    return rc;
+  }
+  rc = batch_apply(b, cfg[best]);
+  if (ms)
+    for (int c = 0; c < POISFFT_BATCH_TUNE_CANDIDATES; c++) ms[c] = t[c];
+  if (chosen) *chosen = best;
+  return rc;
 }
 
 int poisfft_batch_solve_sequential(poisfft_batch* b, void* const phi[], const void* const g[], void* stream) {

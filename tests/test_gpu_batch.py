@@ -1,6 +1,7 @@
 """Batched solves: independent 2D/3D problems of uneven sizes with per-axis
 BCs drawn from all five kinds, solved through one CUDA graph; every problem
-is compared with the FP64 oracle.  Also the tile autotuner."""
+is compared with the FP64 oracle.  Also the per-plan and the batch tile
+autotuners."""
 
 import numpy as np
 import pytest
@@ -88,3 +89,28 @@ def test_autotuned_plan_matches_oracle(pb):
             plan.solve(phi, gd, torch.cuda.current_stream())
             assert plan.check() == pb.OK
             assert O.rel_max_error(phi.cpu().numpy(), ref) < 1e-5
+
+
+def test_batch_autotune_keeps_results(pb):
+    """Each tile configuration the batch tuner tries gives the oracle's
+    answer, and the kept one still does after the graph is re-captured."""
+    probs = _batch(24, 11)
+    gs, refs = _inputs(probs, np.float32)
+    stream = torch.cuda.Stream()
+    with pb.Batch([(p["n"], p["Ls"], p["bcs"]) for p in probs], pb.FD2, pb.F32) as batch:
+        gd = [torch.from_numpy(g).cuda() for g in gs]
+        phis = [torch.full_like(x, float("nan")) for x in gd]
+        torch.cuda.synchronize()
+        chosen, ms = batch.autotune(phis, gd, stream)
+        assert chosen in range(len(pb.Batch.TUNE_CANDIDATES)) and len(ms) == len(pb.Batch.TUNE_CANDIDATES)
+        assert all(t > 0 for t in ms) and ms[chosen] == min(ms)
+        # the tuner's last replays leave the last candidate's solutions in phis
+        for phi, ref in zip(phis, refs):
+            assert O.rel_max_error(phi.cpu().numpy(), ref) < 1e-5
+        for x in phis:
+            x.fill_(float("nan"))
+        batch.solve(phis, gd, stream)
+        stream.synchronize()
+        assert batch.check(stream) == pb.OK
+        for phi, ref, p in zip(phis, refs, probs):
+            assert O.rel_max_error(phi.cpu().numpy(), ref) < 1e-5, p
