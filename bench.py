@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer (e2e) measurement")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the mixed-precision (refined) and FP64 direct solves beside the FP32 one")
     return ap.parse_args()
 
 
@@ -391,8 +393,14 @@ def run_ours(args):
                       method="dense" if npts <= 64 ** 3 else "fft")
         t_chk = time.perf_counter()
         err = O.rel_max_error(phi.cpu().numpy().astype(np.float64), ref)
-        del ref
         print(f"# FP64 check {time.perf_counter() - t_chk:.1f} s", file=sys.stderr)
+
+    # ---- mixed-precision form next to the plain FP32 solve (not the headline)
+    mixed = None
+    if rank == 0 and not args.no_mixed and not f64 and spec["approx"] == pb.FD2:
+        mixed = mixed_form(pb, plan, spec, g_host, ref if err is not None else None, stream, args)
+    if err is not None:
+        del ref
     zero_mode = None
     if rank == 0 and plan_singular(spec["bcs"]):
         zero_mode = {"mean_fp64_gpu": plan.zero_mode_mean(g, stream)}
@@ -412,6 +420,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if f64 else "f32", "data": "synthetic",
             "config": workload_config(args.workload, spec),
             "max_rel_err_vs_fp64": err, "zero_mode": zero_mode, "cufft_comparison": cufft,
+            "mixed_precision": mixed,
             "hbm_frac_step": step_bytes * args.steps / (ms_max / 1e3) / 1e9 / peak,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -434,6 +443,47 @@ def run_ours(args):
 
         dist.destroy_process_group()
     return 0
+
+
+def mixed_form(pb, plan, spec, g_host, ref, stream, args):
+    """FP64 data solved by FP32 FFT solves refined with FP64 residuals of the
+    FD2 operator (poisfft_solve_refined), timed next to the FP64 direct solve
+    of the same problem; errors against the FP64 oracle's solution."""
+    import torch
+
+    g64 = torch.from_numpy(g_host.astype(np.float64)).to("cuda")
+    phi64 = torch.empty_like(g64)
+    ref_d = torch.from_numpy(ref).to("cuda") if ref is not None else None
+    ref_max = float(ref_d.abs().max()) if ref_d is not None else None
+
+    def rel_err(x):
+        return None if ref_d is None else float((x - ref_d).abs().max()) / ref_max
+
+    def timed(fn, steps):
+        for _ in range(max(1, min(args.warmup, 2))):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    out = {"what": "float64 g and phi; FP32 FFT solves of this plan refined with FP64 residuals of the FD2 "
+                   "operator (poisfft_solve_refined), against the FP64 direct solve (FP64 plan) on the same GPU"}
+    steps = max(1, min(args.steps, 5))
+    for k in (1, 2):
+        ms = timed(lambda: plan.solve_refined(phi64, g64, k, stream), steps)
+        out[f"refinements_{k}"] = {"ms_per_solve": ms, "max_rel_err_vs_fp64": rel_err(phi64)}
+    plan64 = pb.Plan(spec["n"], spec["Ls"], spec["bcs"], spec["approx"], pb.F64)
+    ms64 = timed(lambda: plan64.solve(phi64, g64, stream), max(1, min(args.steps, 2)))
+    assert plan64.check(stream) == pb.OK
+    out["fp64_direct"] = {"ms_per_solve": ms64, "max_rel_err_vs_fp64": rel_err(phi64)}
+    plan64.close()
+    del g64, phi64, ref_d
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_batch(args):

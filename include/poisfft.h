@@ -161,6 +161,25 @@ int poisfft_plan_info(const poisfft_plan* plan, int64_t info[4]);
 int poisfft_solve_noalloc(int dims, const int64_t n[], const double L[], const int bc[], int approx, int dtype,
                           void* phi, const void* g, void* stream);
 
+/* Mixed-precision solve by iterative refinement (FP64 data, FP32 FFT
+ * solves).  `plan` is an FP32 plan with approx POISFFT_FD2; g and phi are
+ * distinct device arrays of doubles in the plan's dense layout (8-byte
+ * aligned).  phi_0 = S(g) and phi_{k+1} = phi_k + S(g - L phi_k) for
+ * `refinements` steps (0..8), where S is the plan's FP32 solve (Sec. 2.1
+ * algorithm, Table 4 eigenvalues) and L the second-order FD operator of
+ * Eq. FD2-Laplace on every axis with the boundary ghost values whose
+ * eigenvectors are the Table 2 bases (P wraps; DR phi_-1 = phi_n = 0; DS
+ * phi_-1 = -phi_0, phi_n = -phi_n-1; NS phi_-1 = phi_0, phi_n = phi_n-1; NR
+ * phi_-1 = phi_1, phi_n = phi_n-2).  L phi is evaluated in FP64 and the
+ * residual rounded to FP32 for S.  Each step multiplies the relative error
+ * by about the FP32 solve's (~1e-6) until the FP64 residual's floor, about
+ * cond(L) x 1.1e-16.  Singular problems converge to the zero-mode-free
+ * solution of the FP64 solve.  Allocates one FP32 field on first use
+ * (kept by the plan); asynchronous on `stream`.  Returns POISFFT_OK,
+ * INVALID_ARG (FP64 or spectral plan, phi == g, refinements out of range),
+ * MISALIGNED, ALLOC or CUDA. */
+int poisfft_solve_refined(poisfft_plan* plan, double* phi, const double* g, int refinements, void* stream);
+
 /* Tune the tile shapes of the plan's general-path launches on the device
  * (strided sweeps: w, w/2, w/4 columns per tile; x sweeps: l, l/2, l/4 line
  * pairs per CTA; three timed runs each, the fastest kept).  Allocates two

@@ -71,6 +71,7 @@ EXPORTED = [
     "poisfft_sno_info",
     "poisfft_sno_destroy",
     "poisfft_zero_mode_mean",
+    "poisfft_solve_refined",
 ]
 
 
@@ -126,6 +127,9 @@ def _load():
     for nm in ("poisfft_batch_solve", "poisfft_batch_solve_sequential"):
         getattr(lib, nm).argtypes = [ctypes.c_void_p, vpp, vpp, ctypes.c_void_p]
         getattr(lib, nm).restype = ctypes.c_int
+    lib.poisfft_solve_refined.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                          ctypes.c_void_p]
+    lib.poisfft_solve_refined.restype = ctypes.c_int
     lib.poisfft_batch_autotune.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
     lib.poisfft_batch_autotune.restype = ctypes.c_int
@@ -267,6 +271,14 @@ class Plan:
         rc = solve(self._p, phi, g, stream)
         if rc != OK:
             raise PoisFFTError(rc, "poisfft_solve")
+
+    def solve_refined(self, phi, g, refinements=2, stream=None):
+        """Mixed-precision solve of an FP32 FD2 plan: float64 g in, float64
+        phi out (phi and g distinct), FP32 FFT solves refined with FP64
+        residuals."""
+        rc = lib.poisfft_solve_refined(self._p, _ptr(phi), _ptr(g), int(refinements), _stream(stream))
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_solve_refined")
 
     def solve_strided(self, phi, phi_ld, g, g_ld, stream=None):
         """phi, g: addresses (or tensors) of element (0,0,0); *_ld = (row, plane)

@@ -374,6 +374,7 @@ struct poisfft_plan {
   std::vector<SweepLaunch> sweeps;
   void* stage_g = nullptr;
   void* stage_phi = nullptr;
+  float* refine_r = nullptr;         // FP32 residual / correction of poisfft_solve_refined
   size_t field_bytes = 0;
   bool profiling = false;
   std::vector<cudaEvent_t> events;   // (launches + 1) per profiled solve
@@ -399,6 +400,7 @@ void free_plan(poisfft_plan* p) {
   if (p->zm_count) cudaFree(p->zm_count);
   if (p->stage_g) cudaFree(p->stage_g);
   if (p->stage_phi) cudaFree(p->stage_phi);
+  if (p->refine_r) cudaFree(p->refine_r);
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
   for (int i = 0; i < 3; i++) {
     if (p->ftw[i]) cudaFree(p->ftw[i]);
@@ -1111,10 +1113,10 @@ __global__ void __launch_bounds__(pf::kReduceBlock) zero_mode_kernel(const T* __
 
 }  // namespace
 
-extern "C" int poisfft_zero_mode_mean(poisfft_plan* p, const void* g, double* mean, void* stream) {
-  if (!p || !g || !mean) return POISFFT_ERR_INVALID_ARG;
-  if (!p->singular) return POISFFT_ERR_INVALID_ARG;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+namespace {
+
+// Launches the weighted sum of g (FP32 or FP64 data) into p->zm[0].
+int zero_mode_sum(poisfft_plan* p, const void* g, bool f64, cudaStream_t st) {
   const long long N = (long long)p->nx * p->ny * p->nz;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -1131,22 +1133,205 @@ extern "C" int poisfft_zero_mode_mean(poisfft_plan* p, const void* g, double* me
   const pf::Reduce R{p->zm + 1, p->zm_count};
   const int tx = p->axes[0].bc == POISFFT_NR, ty = p->dims >= 2 && p->axes[1].bc == POISFFT_NR,
             tz = p->dims >= 3 && p->axes[2].bc == POISFFT_NR;
-  if (p->esize == 4)
+  if (!f64)
     zero_mode_kernel<float><<<nb, pf::kReduceBlock, 0, st>>>(static_cast<const float*>(g), p->nx, p->ny, p->nz, tx,
                                                              ty, tz, R, p->zm);
   else
     zero_mode_kernel<double><<<nb, pf::kReduceBlock, 0, st>>>(static_cast<const double*>(g), p->nx, p->ny, p->nz,
                                                               tx, ty, tz, R, p->zm);
-  double sum = 0.0;
-  if (cudaGetLastError() != cudaSuccess ||
-      cudaMemcpyAsync(&sum, p->zm, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return POISFFT_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? POISFFT_OK : POISFFT_ERR_CUDA;
+}
+
+// Sum of the weights of the zero-mode mean (NR axes: n - 1, others n).
+double zero_mode_weight(const poisfft_plan* p) {
   double wsum = 1.0;
   const int nn[3] = {p->nx, p->ny, p->nz};
   for (int a = 0; a < 3; a++) wsum *= (a < p->dims && p->axes[a].bc == POISFFT_NR) ? nn[a] - 1.0 : (double)nn[a];
-  *mean = sum / wsum;
+  return wsum;
+}
+
+}  // namespace
+
+extern "C" int poisfft_zero_mode_mean(poisfft_plan* p, const void* g, double* mean, void* stream) {
+  if (!p || !g || !mean) return POISFFT_ERR_INVALID_ARG;
+  if (!p->singular) return POISFFT_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int rc = zero_mode_sum(p, g, p->esize == 8, st);
+  if (rc != POISFFT_OK) return rc;
+  double sum = 0.0;
+  if (cudaMemcpyAsync(&sum, p->zm, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return POISFFT_ERR_CUDA;
+  *mean = sum / zero_mode_weight(p);
   return POISFFT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision solve by iterative refinement
+// ---------------------------------------------------------------------------
+// FP64 data, FP32 FFT solves: phi_0 = S(g), phi_{k+1} = phi_k + S(g - L phi_k),
+// where S is the FP32 solve of this plan and L the second-order FD operator
+// whose eigenvalues the solve divides by (Eq. FD2-Laplace in every axis, with
+// the boundary ghost values that make the Table 2 bases its eigenvectors:
+// P wraps; DR phi_{-1} = phi_n = 0; DS phi_{-1} = -phi_0, phi_n = -phi_{n-1};
+// NS phi_{-1} = phi_0, phi_n = phi_{n-1}; NR phi_{-1} = phi_1,
+// phi_n = phi_{n-2}).  The residual is formed in FP64 and rounded to FP32
+// for the correction solve; each step multiplies the error by about the FP32
+// solve's relative accuracy, down to the floor set by the FP64 residual
+// (about cond(L) times the FP64 unit roundoff).  For singular problems every
+// S removes the zero mode, so the iteration converges to the solution the
+// FP64 solve gives.
+namespace {
+
+struct Fd2Axis {
+  int n;         // points (1: absent axis)
+  int bc;        // POISFFT_P .. POISFFT_NS
+  long long s;   // element stride
+  double w;      // 1 / dx^2
+};
+
+// phi_{i-1} + phi_{i+1} along one axis with the ghost values of its BC
+// (0 for an absent axis, whose weight is 0)
+__device__ __forceinline__ double fd2_pair(const double* __restrict__ phi, long long idx, int i, const Fd2Axis& a,
+                                           double c) {
+  if (a.n == 1) return 0.0;
+  double l, r;
+  if (i > 0) {
+    l = phi[idx - a.s];
+  } else {
+    switch (a.bc) {
+      case POISFFT_P: l = phi[idx + (long long)(a.n - 1) * a.s]; break;
+      case POISFFT_DR: l = 0.0; break;
+      case POISFFT_DS: l = -c; break;
+      case POISFFT_NS: l = c; break;
+      default: l = phi[idx + a.s]; break;  // NR
+    }
+  }
+  if (i < a.n - 1) {
+    r = phi[idx + a.s];
+  } else {
+    switch (a.bc) {
+      case POISFFT_P: r = phi[idx - (long long)(a.n - 1) * a.s]; break;
+      case POISFFT_DR: r = 0.0; break;
+      case POISFFT_DS: r = -c; break;
+      case POISFFT_NS: r = c; break;
+      default: r = phi[idx - a.s]; break;  // NR
+    }
+  }
+  return l + r;
+}
+
+// Weighted mean of a field that a singular solve removes (device sum times
+// the inverse weight), 0 for nonsingular plans.
+__device__ __forceinline__ double mean_of(const double* zsum, double inv_w) { return zsum ? *zsum * inv_w : 0.0; }
+
+// r = fp32(g - m - L phi) with m the removed mean of g; L phi =
+// sum_a w_a (phi_{i-1} + phi_{i+1}) - 2 (sum_a w_a) phi_i (ten FP64
+// operations per point: GB300 runs FP64 at a small fraction of FP32).
+// grid.x covers x, grid.y strides over the rows y + ny*z.
+__global__ void __launch_bounds__(256) fd2_residual_kernel(const double* __restrict__ phi,
+                                                           const double* __restrict__ g, float* __restrict__ r,
+                                                           Fd2Axis ax, Fd2Axis ay, Fd2Axis az, double w2, int rows,
+                                                           const double* zsum, double inv_w) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= ax.n) return;
+  const double m = mean_of(zsum, inv_w);
+  for (int row = blockIdx.y; row < rows; row += gridDim.y) {
+    const int y = row % ay.n, z = row / ay.n;
+    const long long idx = (long long)row * ax.n + x;
+    const double c = phi[idx];
+    const double lap = fma(ax.w, fd2_pair(phi, idx, x, ax, c),
+                           fma(ay.w, fd2_pair(phi, idx, y, ay, c), fma(az.w, fd2_pair(phi, idx, z, az, c), -w2 * c)));
+    r[idx] = (float)((g[idx] - m) - lap);
+  }
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ g, float* __restrict__ r, long long N, const double* zsum,
+                              double inv_w) {
+  const double m = mean_of(zsum, inv_w);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x)
+    r[e] = (float)(g[e] - m);
+}
+
+// phi -= m (the weighted mean of phi, removed at the end for singular plans)
+__global__ void sub_mean_kernel(double* __restrict__ phi, long long N, const double* zsum, double inv_w) {
+  const double m = mean_of(zsum, inv_w);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x)
+    phi[e] -= m;
+}
+
+// phi = d (first step) or phi += d
+__global__ void add_f32_kernel(double* __restrict__ phi, const float* __restrict__ d, long long N, int first) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x)
+    phi[e] = first ? (double)d[e] : phi[e] + (double)d[e];
+}
+
+}  // namespace
+
+extern "C" int poisfft_solve_refined(poisfft_plan* p, double* phi, const double* g, int refinements, void* stream) {
+  if (!p || !phi || !g || refinements < 0 || refinements > 8 || (const void*)phi == (const void*)g)
+    return POISFFT_ERR_INVALID_ARG;
+  if (p->dtype != POISFFT_F32 || p->approx != POISFFT_FD2) return POISFFT_ERR_INVALID_ARG;
+  if ((uintptr_t)phi % 8 != 0 || (uintptr_t)g % 8 != 0) return POISFFT_ERR_MISALIGNED;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const long long N = (long long)p->nx * p->ny * p->nz;
+  if (!p->refine_r && cudaMalloc(&p->refine_r, (size_t)N * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    p->refine_r = nullptr;
+    return POISFFT_ERR_ALLOC;
+  }
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return POISFFT_ERR_CUDA;
+  Fd2Axis A[3];
+  const int nn[3] = {p->nx, p->ny, p->nz};
+  long long stride = 1;
+  for (int a = 0; a < 3; a++) {
+    A[a].n = nn[a];
+    A[a].bc = p->axes[a].bc;
+    A[a].s = stride;
+    stride *= nn[a];
+    double dx = p->axes[a].L / nn[a];
+    if (A[a].bc == POISFFT_DR) dx = p->axes[a].L / (nn[a] + 1);
+    if (A[a].bc == POISFFT_NR) dx = p->axes[a].L / (nn[a] - 1);
+    A[a].w = a < p->dims ? 1.0 / (dx * dx) : 0.0;
+    if (a >= p->dims) A[a].n = 1;
+  }
+  double w2 = 0.0;
+  for (int a = 0; a < 3; a++) w2 += 2.0 * A[a].w;
+  const unsigned g1 = (unsigned)std::min<long long>((N + 255) / 256, 32LL * sms);
+  const int rows = p->ny * p->nz;
+  const dim3 gr((unsigned)((p->nx + 255) / 256), (unsigned)std::min(rows, 65535));
+  // singular problems: the null-space component (the weighted mean of g,
+  // which every solve removes) is subtracted in FP64 first, so that the
+  // FP32 residuals carry only the part the corrections resolve
+  const double* zsum = nullptr;
+  double inv_w = 0.0;
+  int rc = POISFFT_OK;
+  if (p->singular) {
+    if ((rc = zero_mode_sum(p, g, true, st)) != POISFFT_OK) return rc;
+    zsum = p->zm;
+    inv_w = 1.0 / zero_mode_weight(p);
+  }
+  to_f32_kernel<<<g1, 256, 0, st>>>(g, p->refine_r, N, zsum, inv_w);
+  if (cudaGetLastError() != cudaSuccess) return POISFFT_ERR_CUDA;
+  rc = poisfft_solve(p, p->refine_r, p->refine_r, stream);
+  if (rc != POISFFT_OK) return rc;
+  add_f32_kernel<<<g1, 256, 0, st>>>(phi, p->refine_r, N, 1);
+  for (int k = 0; k < refinements; k++) {
+    fd2_residual_kernel<<<gr, 256, 0, st>>>(phi, g, p->refine_r, A[0], A[1], A[2], w2, rows, zsum, inv_w);
+    if (cudaGetLastError() != cudaSuccess) return POISFFT_ERR_CUDA;
+    rc = poisfft_solve(p, p->refine_r, p->refine_r, stream);
+    if (rc != POISFFT_OK) return rc;
+    add_f32_kernel<<<g1, 256, 0, st>>>(phi, p->refine_r, N, 0);
+  }
+  // the residual cannot see a constant (L 1 = 0): the FP32 rounding of the
+  // solves' zero modes stays in phi unless its weighted mean is removed in FP64
+  if (p->singular) {
+    if ((rc = zero_mode_sum(p, phi, true, st)) != POISFFT_OK) return rc;
+    sub_mean_kernel<<<g1, 256, 0, st>>>(phi, N, p->zm, inv_w);
+  }
+  return cudaGetLastError() == cudaSuccess ? POISFFT_OK : POISFFT_ERR_CUDA;
 }
 
 // ---------------------------------------------------------------------------
