@@ -1081,8 +1081,8 @@ int poisfft_plan_info(const poisfft_plan* p, int64_t info[4]) {
 // ---------------------------------------------------------------------------
 // The solve sets the all-zero spectral coefficient to 0, i.e. removes the
 // weighted mean of g (weights 1/2 at both ends of NR axes, 1 elsewhere).
-// Per-thread sums are compensated (Kahan) in the data precision, the
-// cross-thread sum is FP64 and deterministic.
+// Per-thread sums are compensated (Kahan) for FP32 data and plain for FP64
+// data; the cross-thread sum is FP64 and deterministic.
 namespace {
 
 template <typename T>
@@ -1100,10 +1100,17 @@ __global__ void __launch_bounds__(pf::kReduceBlock) zero_mode_kernel(const T* __
     const T* row = g + r * nx;
     for (int x = threadIdx.x; x < nx; x += blockDim.x) {
       const T w = (trap_x && (x == 0 || x == nx - 1)) ? T(0.5) * wr : wr;
-      const T yv = w * row[x] - c;
-      const T t = s + yv;
-      c = (t - s) - yv;
-      s = t;
+      if constexpr (sizeof(T) == 8) {
+        // FP64 data: a plain FP64 sum of a few thousand terms per thread is
+        // accurate to ~1e-13 of the sum of magnitudes, and GB300's FP64 rate
+        // makes the compensated form four times as expensive
+        s = fma(w, row[x], s);
+      } else {
+        const T yv = w * row[x] - c;
+        const T t = s + yv;
+        c = (t - s) - yv;
+        s = t;
+      }
     }
   }
   const double v[1] = {(double)s - (double)c};
