@@ -55,12 +55,14 @@ inline __host__ __device__ FastDiv make_fastdiv(uint32_t d) {
   const uint64_t m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;  // < 2^32 because 2^l < 2d
   return FastDiv{d, (uint32_t)m, l < 1 ? l : 1, l > 1 ? l - 1 : 0};
 }
-#ifdef __CUDACC__
-__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+__host__ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+#ifdef __CUDA_ARCH__
   const uint32_t t = __umulhi(n, f.m);
+#else
+  const uint32_t t = (uint32_t)(((uint64_t)n * f.m) >> 32);
+#endif
   return (t + ((n - t) >> f.s1)) >> f.s2;
 }
-#endif
 
 struct FftDesc {
   int M;                  // FFT length
