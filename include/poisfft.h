@@ -40,8 +40,12 @@ typedef enum { POISFFT_SPECTRAL = 0, POISFFT_FD2 = 1 } poisfft_approx;
 /* Storage and arithmetic type of phi and g.  The paper's library offers single
  * and double precision solver objects (Sec. 3).  F32: float arrays, FP32
  * arithmetic with tables rounded once from FP64.  F64: double arrays and
- * arithmetic. */
-typedef enum { POISFFT_F32 = 0, POISFFT_F64 = 1 } poisfft_dtype;
+ * arithmetic.  MIXED: double arrays; the transforms run in FP32 (the F32
+ * kernels) and the result is refined with residuals of the FD2 operator
+ * (Eq. FD2-Laplace) formed in FP64, so the answer reaches the F64 solve's
+ * accuracy class at a fraction of its cost (see poisfft_solve_refined, which
+ * a MIXED plan's poisfft_solve runs).  MIXED needs approx POISFFT_FD2. */
+typedef enum { POISFFT_F32 = 0, POISFFT_F64 = 1, POISFFT_MIXED = 2 } poisfft_dtype;
 
 /* Status codes. */
 enum {
@@ -67,11 +71,12 @@ typedef struct poisfft_plan poisfft_plan;  /* opaque; owned by the library */
  *   bc     : bc[2*a] and bc[2*a+1] = the two faces of axis a (low, high).
  *            Both faces must be equal (the transforms of Table 2 are defined
  *            per axis); every per-axis combination is accepted.
- *   approx : poisfft_approx.   dtype : poisfft_dtype.
+ *   approx : poisfft_approx.   dtype : poisfft_dtype; MIXED with approx
+ *            SPECTRAL returns POISFFT_ERR_NOT_IMPLEMENTED.
  * Allocates the device workspace (about one field of the plan's dtype plus
- * padding) and FP64-derived tables on the current CUDA device.  All
- * argument checks happen before any CUDA call, so argument errors are
- * reported even without a GPU.
+ * padding; one FP32 field for MIXED) and FP64-derived tables on the current
+ * CUDA device.  All argument checks happen before any CUDA call, so
+ * argument errors are reported even without a GPU.
  * FP32 plans of 2 or 3 dimensions with every length in {64, 128, 256, 512,
  * 1024} use specialised two-pass kernels when x is periodic and y/z are
  * periodic or staggered (Dirichlet or Neumann), or when x, y and z are all
@@ -90,8 +95,17 @@ int poisfft_plan_create(poisfft_plan** out, int dims, const int64_t n[], const d
  * owns one workspace, so one plan must not run on two streams at once.
  * For singular problems (every axis P, NR or NS) the component of g in the
  * null space is removed (the all-zero spectral coefficient is set to 0), so
- * phi has zero mean (trapezoid-weighted along NR axes). */
+ * phi has zero mean (trapezoid-weighted along NR axes).
+ * MIXED plans: phi and g are arrays of doubles (8-byte aligned) and must be
+ * distinct; the call is poisfft_solve_refined(plan, phi, g, k, stream) with
+ * k = 2 refinements unless poisfft_plan_set_refinements chose another k. */
 int poisfft_solve(poisfft_plan* plan, void* phi, const void* g, void* stream);
+
+/* Refinement steps (0..8) that poisfft_solve runs on a MIXED plan.  Each step
+ * costs one FP32 solve plus an FP64 residual; 1 step gives about 5e-11 and 2
+ * steps about 4e-14 relative error on a 1024^3 FD2 problem.  Returns
+ * POISFFT_ERR_INVALID_ARG for other plans or k out of range. */
+int poisfft_plan_set_refinements(poisfft_plan* plan, int refinements);
 
 /* The same solve on arrays that are part of larger arrays, e.g. fields with
  * ghost cells (Sec. 3: the right-hand side and the solution can be a subset
@@ -101,7 +115,8 @@ int poisfft_solve(poisfft_plan* plan, void* phi, const void* g, void* stream);
  *   axes the plan does not have are ignored.
  * Elements outside the grid (ghost cells) are neither read nor written.
  * phi == g with equal strides is allowed.  POISFFT_ERR_INVALID_ARG for
- * strides that would overlap rows or planes. */
+ * strides that would overlap rows or planes; POISFFT_ERR_NOT_IMPLEMENTED for
+ * MIXED plans. */
 int poisfft_solve_strided(poisfft_plan* plan, void* phi, const int64_t phi_ld[2], const void* g, const int64_t g_ld[2],
                           void* stream);
 
@@ -152,14 +167,25 @@ int poisfft_plan_info(const poisfft_plan* plan, int64_t info[4]);
  *     call clears what must start at zero.  Calls that overlap on the GPU
  *     (other streams, other host threads) race on the array: serialise them.
  *   - Tables are copied from pageable host memory, so the call waits for
- *     the work already queued on `stream` before it returns.
- * x non-periodic together with a periodic y or z returns
- * POISFFT_ERR_NOT_IMPLEMENTED here (poisfft_solve handles it).
- * Returns the status codes of poisfft_plan_create / poisfft_solve; check
- * the kernels' bounded waits with cudaStreamSynchronize (no plan exists
- * for poisfft_check). */
+ *     the work already queued on `stream` before it returns.  Those copies
+ *     read host memory that does not outlive the call, so while `stream`
+ *     is being captured the call returns POISFFT_ERR_NOT_IMPLEMENTED and
+ *     enqueues nothing.
+ * x non-periodic together with a periodic y or z, and dtype MIXED, return
+ * POISFFT_ERR_NOT_IMPLEMENTED here (poisfft_solve handles them).
+ * Returns the status codes of poisfft_plan_create / poisfft_solve.  A
+ * bounded device wait that gives up does not make the stream fail: it sets
+ * the error flag in the shared array, which poisfft_noalloc_check reads. */
 int poisfft_solve_noalloc(int dims, const int64_t n[], const double L[], const int bc[], int approx, int dtype,
                           void* phi, const void* g, void* stream);
+
+/* Error flag of poisfft_solve_noalloc on the current device (no paper
+ * counterpart).  Synchronises `stream`, reads the flag word at the start of
+ * the shared array and clears it.  Every poisfft_solve_noalloc call clears
+ * the flag when it starts, so check after each call whose result matters.
+ * Returns POISFFT_OK, POISFFT_ERR_TIMEOUT (a kernel's bounded wait gave up:
+ * phi is not valid) or POISFFT_ERR_CUDA.  Allocates nothing. */
+int poisfft_noalloc_check(void* stream);
 
 /* Mixed-precision solve by iterative refinement (FP64 data, FP32 FFT
  * solves).  `plan` is an FP32 plan with approx POISFFT_FD2; g and phi are
@@ -174,10 +200,10 @@ int poisfft_solve_noalloc(int dims, const int64_t n[], const double L[], const i
  * residual rounded to FP32 for S.  Each step multiplies the relative error
  * by about the FP32 solve's (~1e-6) until the FP64 residual's floor, about
  * cond(L) x 1.1e-16.  Singular problems converge to the zero-mode-free
- * solution of the FP64 solve.  Allocates one FP32 field on first use
- * (kept by the plan); asynchronous on `stream`.  Returns POISFFT_OK,
- * INVALID_ARG (FP64 or spectral plan, phi == g, refinements out of range),
- * MISALIGNED, ALLOC or CUDA. */
+ * solution of the FP64 solve.  `plan` may also be a MIXED plan.  Allocates
+ * one FP32 field on first use (kept by the plan); asynchronous on `stream`.
+ * Returns POISFFT_OK, INVALID_ARG (FP64 or spectral plan, phi == g,
+ * refinements out of range), MISALIGNED, ALLOC or CUDA. */
 int poisfft_solve_refined(poisfft_plan* plan, double* phi, const double* g, int refinements, void* stream);
 
 /* Tune the tile shapes of the plan's general-path launches on the device
@@ -191,9 +217,9 @@ int poisfft_plan_autotune(poisfft_plan* plan, void* stream);
 /* ---- Batched solves (many independent problems; no paper counterpart) ----
  * poisfft_batch_create: one plan per problem i with dims[i], n[3i..3i+2],
  *   L[3i..3i+2], bc[6i..6i+5] (entries beyond dims[i] ignored), a shared
- *   approx and dtype, with the default tile shapes (poisfft_batch_autotune
- *   tunes them in the batch's own setting).  Fails with the first failing
- *   plan's status.
+ *   approx and dtype (F32 or F64; MIXED returns NOT_IMPLEMENTED), with the
+ *   default tile shapes (poisfft_batch_autotune tunes them in the batch's
+ *   own setting).  Fails with the first failing plan's status.
  * poisfft_batch_solve: solves every problem (phi[i], g[i] as in
  *   poisfft_solve) on `stream`.  The problems' launches run on forked
  *   streams inside one CUDA graph, captured on the first call and replayed

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libpoisfft.so")
 P, DR, DS, NR, NS = 0, 1, 2, 3, 4
 PCG_F64, PCG_MIXED = 0, 1
 SPECTRAL, FD2 = 0, 1
-F32, F64 = 0, 1
+F32, F64, MIXED = 0, 1, 2
 
 OK = 0
 ERR_INVALID_ARG = -1
@@ -44,6 +44,8 @@ EXPORTED = [
     "poisfft_profile_read",
     "poisfft_launch_info",
     "poisfft_solve_noalloc",
+    "poisfft_noalloc_check",
+    "poisfft_plan_set_refinements",
     "poisfft_solve_strided",
     "poisfft_plan_autotune",
     "poisfft_batch_create",
@@ -114,6 +116,10 @@ def _load():
                                           ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.poisfft_solve_noalloc.restype = ctypes.c_int
+    lib.poisfft_noalloc_check.argtypes = [ctypes.c_void_p]
+    lib.poisfft_noalloc_check.restype = ctypes.c_int
+    lib.poisfft_plan_set_refinements.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.poisfft_plan_set_refinements.restype = ctypes.c_int
     lib.poisfft_solve_strided.argtypes = [ctypes.c_void_p, ctypes.c_void_p, i64p, ctypes.c_void_p, i64p,
                                           ctypes.c_void_p]
     lib.poisfft_solve_strided.restype = ctypes.c_int
@@ -238,6 +244,12 @@ def solve_noalloc(n, L, bc, approx, dtype, phi, g, stream=None):
                                      _stream(stream))
 
 
+def noalloc_check(stream=None):
+    """poisfft_noalloc_check: synchronise `stream`, read and clear the error
+    flag of poisfft_solve_noalloc.  Returns the status code."""
+    return lib.poisfft_noalloc_check(_stream(stream))
+
+
 def check(plan, stream=None):
     return lib.poisfft_check(plan, _stream(stream))
 
@@ -271,6 +283,12 @@ class Plan:
         rc = solve(self._p, phi, g, stream)
         if rc != OK:
             raise PoisFFTError(rc, "poisfft_solve")
+
+    def set_refinements(self, refinements):
+        """Refinement steps of poisfft_solve on a MIXED plan."""
+        rc = lib.poisfft_plan_set_refinements(self._p, int(refinements))
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_plan_set_refinements")
 
     def solve_refined(self, phi, g, refinements=2, stream=None):
         """Mixed-precision solve of an FP32 FD2 plan: float64 g in, float64

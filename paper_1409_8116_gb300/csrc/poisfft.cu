@@ -375,6 +375,7 @@ struct poisfft_plan {
   void* stage_g = nullptr;
   void* stage_phi = nullptr;
   float* refine_r = nullptr;         // FP32 residual / correction of poisfft_solve_refined
+  int refinements = 2;               // POISFFT_MIXED plans: refinement steps of poisfft_solve
   size_t field_bytes = 0;
   bool profiling = false;
   std::vector<cudaEvent_t> events;   // (launches + 1) per profiled solve
@@ -784,6 +785,185 @@ int enqueue(poisfft_plan* p, void* phi, const void* g, cudaStream_t st) {
   return enqueue<T>(p, phi, g, st, FieldStrides{nx, nxy, nx, nxy});
 }
 
+// ---------------------------------------------------------------------------
+// host-side planning shared by poisfft_plan_create and poisfft_solve_noalloc
+// ---------------------------------------------------------------------------
+struct PlanArgs {
+  int dims = 0;
+  int bc[3] = {POISFFT_P, POISFFT_P, POISFFT_P};
+  long long n[3] = {1, 1, 1};
+  double L[3] = {1.0, 1.0, 1.0};
+  int approx = POISFFT_FD2;
+  int dtype = POISFFT_F32;
+};
+
+// Argument checks of the plan-creating calls (no CUDA call).
+int validate_args(int dims, const int64_t n[], const double L[], const int bc[], int approx, int dtype,
+                  PlanArgs& a) {
+  if (!n || !L || !bc || dims < 1 || dims > 3) return POISFFT_ERR_INVALID_ARG;
+  if (approx != POISFFT_SPECTRAL && approx != POISFFT_FD2) return POISFFT_ERR_INVALID_ARG;
+  if (dtype != POISFFT_F32 && dtype != POISFFT_F64 && dtype != POISFFT_MIXED) return POISFFT_ERR_INVALID_ARG;
+  a.dims = dims;
+  a.approx = approx;
+  a.dtype = dtype;
+  for (int ax = 0; ax < dims; ax++) {
+    if (n[ax] < 1 || n[ax] > (1 << 24)) return POISFFT_ERR_INVALID_ARG;
+    if (!(L[ax] > 0.0) || !isfinite(L[ax])) return POISFFT_ERR_INVALID_ARG;
+    const int b0 = bc[2 * ax], b1 = bc[2 * ax + 1];
+    if (b0 < POISFFT_P || b0 > POISFFT_NS || b1 < POISFFT_P || b1 > POISFFT_NS) return POISFFT_ERR_INVALID_ARG;
+    if (b0 != b1) return POISFFT_ERR_UNSUPPORTED_BC;
+    if (b0 == POISFFT_NR && n[ax] < 2) return POISFFT_ERR_INVALID_ARG;
+    a.bc[ax] = b0;
+    a.n[ax] = n[ax];
+    a.L[ax] = L[ax];
+  }
+  // the mixed form refines with the FD2 operator (Eq. FD2-Laplace)
+  if (dtype == POISFFT_MIXED && approx != POISFFT_FD2) return POISFFT_ERR_NOT_IMPLEMENTED;
+  if ((double)a.n[0] * a.n[1] * a.n[2] > 4.0e10) return POISFFT_ERR_UNSUPPORTED_SIZE;
+  return POISFFT_OK;
+}
+
+// Everything of a plan that needs no device: axes with their FP64 tables,
+// the workspace shape, tiles and the sweep sequence.  general_only plans
+// use the general kernels only and no separate pair-divide pass, so their
+// sweeps are x sweeps (kind 0) and strided sweeps (kind 1) only; x
+// non-periodic with a periodic y or z then returns
+// POISFFT_ERR_NOT_IMPLEMENTED.  No CUDA call.
+int plan_host(poisfft_plan* p, const PlanArgs& a, bool general_only) {
+  const int dims = a.dims;
+  // x periodic -> half-spectrum workspace; otherwise the real transformed
+  // field viewed as complex pairs.  x non-periodic with a periodic y or z
+  // divides in a separate pass that pairs k with -k (PairDivideArgs).
+  const bool xper = a.bc[0] == POISFFT_P;
+  bool any_per_yz = false;
+  for (int ax = 1; ax < dims; ax++) any_per_yz |= a.bc[ax] == POISFFT_P;
+  if (general_only && !xper && any_per_yz) return POISFFT_ERR_NOT_IMPLEMENTED;
+  p->dims = dims;
+  p->dtype = a.dtype;
+  p->approx = a.approx;
+  p->nx = (int)a.n[0];
+  p->ny = (int)a.n[1];
+  p->nz = (int)a.n[2];
+  p->esize = a.dtype == POISFFT_F64 ? 8 : 4;  // the mixed form solves in FP32
+  p->r2c = xper ? 1 : 0;
+  const int emax = p->esize == 4 ? 40 : 16;
+  bool sing = true;
+  for (int ax = 0; ax < 3; ax++) {
+    const bool null_axis = ax >= dims;
+    const int rc = build_axis(p->axes[ax], a.bc[ax], (int)a.n[ax], a.L[ax], a.approx, emax, null_axis);
+    if (rc != POISFFT_OK) return rc;
+    if (!null_axis) sing = sing && (a.bc[ax] == POISFFT_P || a.bc[ax] == POISFFT_NR || a.bc[ax] == POISFFT_NS);
+  }
+  p->singular = sing ? 1 : 0;
+  p->ncols = p->r2c ? p->nx / 2 + 1 : (p->nx + 1) / 2;
+  p->pitch = (p->ncols + 1) / 2 * 2;
+  p->field_bytes = (size_t)p->nx * p->ny * p->nz * p->esize;
+  p->ws_bytes = (size_t)p->pitch * 2 * p->esize * p->ny * p->nz;
+
+  // sweep sequence and tiling
+  std::vector<SweepLaunch> sw;
+  SweepLaunch Ls;
+  int rc;
+  p->fast = !general_only && fast_eligible(p);
+  if (p->fast) {
+    plan_fast_x(p, fast::FM_FWD, Ls);
+    sw.push_back(Ls);
+    if (dims == 3) { plan_fast_strided(p, 1, fast::FM_FWD, Ls); sw.push_back(Ls); }
+    plan_fast_strided(p, dims == 3 ? 2 : 1, fast::FM_FUSED, Ls);
+    sw.push_back(Ls);
+    if (dims == 3) { plan_fast_strided(p, 1, fast::FM_INV, Ls); sw.push_back(Ls); }
+    plan_fast_x(p, fast::FM_INV, Ls);
+    sw.push_back(Ls);
+  } else if (!xper && any_per_yz) {
+    if ((rc = plan_x_sweep(p, 0, Ls)) != POISFFT_OK) return rc;
+    sw.push_back(Ls);
+    for (int ax = 1; ax < dims; ax++) {
+      if ((rc = plan_strided_sweep(p, ax, 0, Ls)) != POISFFT_OK) return rc;
+      sw.push_back(Ls);
+    }
+    memset(&Ls, 0, sizeof(Ls));
+    Ls.kind = 4;
+    PairDivideArgs& d = Ls.pda;
+    d.pitch = p->pitch;
+    d.ncols = p->ncols;
+    d.dncols = make_fastdiv((uint32_t)p->ncols);
+    if ((long long)p->ncols * p->ny > 0x7fffffffLL) return POISFFT_ERR_UNSUPPORTED_SIZE;
+    d.nx = p->nx;
+    d.ny = p->ny;
+    d.nz = p->nz;
+    d.per_y = dims >= 2 && a.bc[1] == POISFFT_P;
+    d.per_z = dims >= 3 && a.bc[2] == POISFFT_P;
+    double sc = 1.0;
+    for (int i = 0; i < 3; i++) sc *= p->axes[i].scale;
+    d.scale = sc;
+    d.singular = p->singular;
+    Ls.bytes = 2LL * p->ncols * (long long)p->ny * p->nz * (long long)(2 * p->esize);
+    sw.push_back(Ls);
+    for (int ax = dims - 1; ax >= 1; ax--) {
+      if ((rc = plan_strided_sweep(p, ax, 1, Ls)) != POISFFT_OK) return rc;
+      sw.push_back(Ls);
+    }
+    if ((rc = plan_x_sweep(p, 1, Ls)) != POISFFT_OK) return rc;
+    sw.push_back(Ls);
+  } else {
+    if ((rc = plan_x_sweep(p, 0, Ls)) != POISFFT_OK) return rc;
+    sw.push_back(Ls);
+    const int fused_axis = dims == 3 ? 2 : 1;
+    if (dims == 3) {
+      if ((rc = plan_strided_sweep(p, 1, 0, Ls)) != POISFFT_OK) return rc;
+      sw.push_back(Ls);
+    }
+    if ((rc = plan_strided_sweep(p, fused_axis, 2, Ls)) != POISFFT_OK) return rc;
+    sw.push_back(Ls);
+    if (dims == 3) {
+      if ((rc = plan_strided_sweep(p, 1, 1, Ls)) != POISFFT_OK) return rc;
+      sw.push_back(Ls);
+    }
+    if ((rc = plan_x_sweep(p, 1, Ls)) != POISFFT_OK) return rc;
+    sw.push_back(Ls);
+  }
+  p->sweeps = sw;
+  return POISFFT_OK;
+}
+
+// Point the general-path launches at the plan's device buffers (the sweeps
+// are planned before the buffers exist).
+void patch_general(poisfft_plan* p) {
+  for (auto& L : p->sweeps) {
+    if (L.kind == 0) {
+      L.xa.tables = p->tables[0];
+      L.xa.perm = p->perm[0];
+      L.xa.ws = p->ws;
+      L.xa.err = p->err;
+    } else if (L.kind == 4) {
+      L.pda.data = p->ws;
+      L.pda.lam_x = p->lam[0];
+      L.pda.lam_y = p->lam[1];
+      L.pda.lam_z = p->lam[2];
+    } else if (L.kind == 1) {
+      const int a = L.sa.axis_dim;
+      L.sa.tables = p->tables[a];
+      L.sa.perm = p->perm[a];
+      L.sa.data = p->ws;
+      L.sa.lam_in = p->lam[0];
+      L.sa.lam_ax = p->lam[a];
+      L.sa.lam_out = p->lam[a == 1 ? 2 : 1];
+      L.sa.err = p->err;
+    }
+  }
+}
+
+// The FFT solve of the plan's kernels on arrays of its kernel precision.
+int solve_core(poisfft_plan* p, void* phi, const void* g, cudaStream_t st) {
+  if (((uintptr_t)phi % p->esize) != 0 || ((uintptr_t)g % p->esize) != 0) return POISFFT_ERR_MISALIGNED;
+  return p->esize == 4 ? enqueue<float>(p, phi, g, st) : enqueue<double>(p, phi, g, st);
+}
+
+// Bytes of one caller field (the mixed form takes doubles).
+size_t user_field_bytes(const poisfft_plan* p) {
+  return (size_t)p->nx * p->ny * p->nz * (p->dtype == POISFFT_MIXED ? 8 : p->esize);
+}
+
 }  // namespace
 
 extern "C" {
@@ -807,118 +987,12 @@ int poisfft_plan_create(poisfft_plan** out, int dims, const int64_t n[], const d
                         int approx, int dtype) {
   if (!out) return POISFFT_ERR_INVALID_ARG;
   *out = nullptr;
-  if (!n || !L || !bc || dims < 1 || dims > 3) return POISFFT_ERR_INVALID_ARG;
-  if (approx != POISFFT_SPECTRAL && approx != POISFFT_FD2) return POISFFT_ERR_INVALID_ARG;
-  if (dtype != POISFFT_F32 && dtype != POISFFT_F64) return POISFFT_ERR_INVALID_ARG;
-  int bca[3] = {POISFFT_P, POISFFT_P, POISFFT_P};
-  long long nn[3] = {1, 1, 1};
-  double LL[3] = {1.0, 1.0, 1.0};
-  for (int a = 0; a < dims; a++) {
-    if (n[a] < 1 || n[a] > (1 << 24)) return POISFFT_ERR_INVALID_ARG;
-    if (!(L[a] > 0.0) || !isfinite(L[a])) return POISFFT_ERR_INVALID_ARG;
-    const int b0 = bc[2 * a], b1 = bc[2 * a + 1];
-    if (b0 < POISFFT_P || b0 > POISFFT_NS || b1 < POISFFT_P || b1 > POISFFT_NS) return POISFFT_ERR_INVALID_ARG;
-    if (b0 != b1) return POISFFT_ERR_UNSUPPORTED_BC;
-    if (b0 == POISFFT_NR && n[a] < 2) return POISFFT_ERR_INVALID_ARG;
-    bca[a] = b0;
-    nn[a] = n[a];
-    LL[a] = L[a];
-  }
-  if ((double)nn[0] * nn[1] * nn[2] > 4.0e10) return POISFFT_ERR_UNSUPPORTED_SIZE;
-  // x periodic -> half-spectrum workspace; otherwise the real transformed
-  // field viewed as complex pairs.  x non-periodic with a periodic y or z
-  // divides in a separate pass that pairs k with -k (PairDivideArgs).
-  const bool xper = bca[0] == POISFFT_P;
-  bool any_per_yz = false;
-  for (int a = 1; a < dims; a++) any_per_yz |= bca[a] == POISFFT_P;
-
+  PlanArgs args;
+  int rc = validate_args(dims, n, L, bc, approx, dtype, args);
+  if (rc != POISFFT_OK) return rc;
   poisfft_plan* p = new (std::nothrow) poisfft_plan();
   if (!p) return POISFFT_ERR_ALLOC;
-  p->dims = dims;
-  p->dtype = dtype;
-  p->approx = approx;
-  p->nx = (int)nn[0];
-  p->ny = (int)nn[1];
-  p->nz = (int)nn[2];
-  p->esize = dtype == POISFFT_F32 ? 4 : 8;
-  p->r2c = xper ? 1 : 0;
-  const int emax = dtype == POISFFT_F32 ? 40 : 16;
-  bool sing = true;
-  for (int a = 0; a < 3; a++) {
-    const bool null_axis = a >= dims;
-    int rc = build_axis(p->axes[a], bca[a], (int)nn[a], LL[a], approx, emax, null_axis);
-    if (rc != POISFFT_OK) { free_plan(p); return rc; }
-    if (!null_axis) sing = sing && (bca[a] == POISFFT_P || bca[a] == POISFFT_NR || bca[a] == POISFFT_NS);
-  }
-  p->singular = sing ? 1 : 0;
-  p->ncols = p->r2c ? p->nx / 2 + 1 : (p->nx + 1) / 2;
-  p->pitch = (p->ncols + 1) / 2 * 2;
-  p->field_bytes = (size_t)p->nx * p->ny * p->nz * p->esize;
-  p->ws_bytes = (size_t)p->pitch * 2 * p->esize * p->ny * p->nz;
-
-  // sweep sequence and tiling (host only, before any CUDA call)
-  std::vector<SweepLaunch> sw;
-  SweepLaunch Ls;
-  int rc;
-  p->fast = fast_eligible(p);
-  if (p->fast) {
-    plan_fast_x(p, fast::FM_FWD, Ls);
-    sw.push_back(Ls);
-    if (dims == 3) { plan_fast_strided(p, 1, fast::FM_FWD, Ls); sw.push_back(Ls); }
-    plan_fast_strided(p, dims == 3 ? 2 : 1, fast::FM_FUSED, Ls);
-    sw.push_back(Ls);
-    if (dims == 3) { plan_fast_strided(p, 1, fast::FM_INV, Ls); sw.push_back(Ls); }
-    plan_fast_x(p, fast::FM_INV, Ls);
-    sw.push_back(Ls);
-  } else if (!xper && any_per_yz) {
-    if ((rc = plan_x_sweep(p, 0, Ls)) != POISFFT_OK) { free_plan(p); return rc; }
-    sw.push_back(Ls);
-    for (int a = 1; a < dims; a++) {
-      if ((rc = plan_strided_sweep(p, a, 0, Ls)) != POISFFT_OK) { free_plan(p); return rc; }
-      sw.push_back(Ls);
-    }
-    memset(&Ls, 0, sizeof(Ls));
-    Ls.kind = 4;
-    PairDivideArgs& d = Ls.pda;
-    d.pitch = p->pitch;
-    d.ncols = p->ncols;
-    d.dncols = make_fastdiv((uint32_t)p->ncols);
-    if ((long long)p->ncols * p->ny > 0x7fffffffLL) { free_plan(p); return POISFFT_ERR_UNSUPPORTED_SIZE; }
-    d.nx = p->nx;
-    d.ny = p->ny;
-    d.nz = p->nz;
-    d.per_y = dims >= 2 && bca[1] == POISFFT_P;
-    d.per_z = dims >= 3 && bca[2] == POISFFT_P;
-    double sc = 1.0;
-    for (int i = 0; i < 3; i++) sc *= p->axes[i].scale;
-    d.scale = sc;
-    d.singular = p->singular;
-    Ls.bytes = 2LL * p->ncols * (long long)p->ny * p->nz * (long long)(2 * p->esize);
-    sw.push_back(Ls);
-    for (int a = dims - 1; a >= 1; a--) {
-      if ((rc = plan_strided_sweep(p, a, 1, Ls)) != POISFFT_OK) { free_plan(p); return rc; }
-      sw.push_back(Ls);
-    }
-    if ((rc = plan_x_sweep(p, 1, Ls)) != POISFFT_OK) { free_plan(p); return rc; }
-    sw.push_back(Ls);
-  } else {
-  if ((rc = plan_x_sweep(p, 0, Ls)) != POISFFT_OK) { free_plan(p); return rc; }
-  sw.push_back(Ls);
-  const int fused_axis = dims == 3 ? 2 : 1;
-  if (dims == 3) {
-    if ((rc = plan_strided_sweep(p, 1, 0, Ls)) != POISFFT_OK) { free_plan(p); return rc; }
-    sw.push_back(Ls);
-  }
-  if ((rc = plan_strided_sweep(p, fused_axis, 2, Ls)) != POISFFT_OK) { free_plan(p); return rc; }
-  sw.push_back(Ls);
-  if (dims == 3) {
-    if ((rc = plan_strided_sweep(p, 1, 1, Ls)) != POISFFT_OK) { free_plan(p); return rc; }
-    sw.push_back(Ls);
-  }
-  if ((rc = plan_x_sweep(p, 1, Ls)) != POISFFT_OK) { free_plan(p); return rc; }
-  sw.push_back(Ls);
-  }
-  p->sweeps = sw;
+  if ((rc = plan_host(p, args, false)) != POISFFT_OK) { free_plan(p); return rc; }
 
   // device resources
   if (cudaMalloc(&p->err, sizeof(int)) != cudaSuccess) { cudaGetLastError(); free_plan(p); return POISFFT_ERR_CUDA; }
@@ -929,29 +1003,7 @@ int poisfft_plan_create(poisfft_plan** out, int dims, const int64_t n[], const d
   for (int a = 0; p->fast && a < dims && rc == POISFFT_OK; a++) rc = fast_upload_axis(p, a);
   if (rc != POISFFT_OK) { cudaGetLastError(); free_plan(p); return rc; }
   if (p->fast) patch_fast(p);
-  // the sweeps were planned before the buffers existed: patch the pointers
-  for (auto& L : p->sweeps) {
-    if (L.kind == 0) {
-      L.xa.tables = p->tables[0];
-      L.xa.perm = p->perm[0];
-      L.xa.ws = p->ws;
-      L.xa.err = p->err;
-    } else if (L.kind == 4) {
-      L.pda.data = p->ws;
-      L.pda.lam_x = p->lam[0];
-      L.pda.lam_y = p->lam[1];
-      L.pda.lam_z = p->lam[2];
-    } else if (L.kind == 1) {
-      const int a = L.sa.axis_dim;
-      L.sa.tables = p->tables[a];
-      L.sa.perm = p->perm[a];
-      L.sa.data = p->ws;
-      L.sa.lam_in = p->lam[0];
-      L.sa.lam_ax = p->lam[a];
-      L.sa.lam_out = p->lam[a == 1 ? 2 : 1];
-      L.sa.err = p->err;
-    }
-  }
+  patch_general(p);
   if ((rc = encode_maps(p)) != POISFFT_OK) { free_plan(p); return rc; }
   *out = p;
   return POISFFT_OK;
@@ -959,14 +1011,21 @@ int poisfft_plan_create(poisfft_plan** out, int dims, const int64_t n[], const d
 
 int poisfft_solve(poisfft_plan* p, void* phi, const void* g, void* stream) {
   if (!p || !phi || !g) return POISFFT_ERR_INVALID_ARG;
-  if (((uintptr_t)phi % p->esize) != 0 || ((uintptr_t)g % p->esize) != 0) return POISFFT_ERR_MISALIGNED;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  return p->esize == 4 ? enqueue<float>(p, phi, g, st) : enqueue<double>(p, phi, g, st);
+  if (p->dtype == POISFFT_MIXED)
+    return poisfft_solve_refined(p, static_cast<double*>(phi), static_cast<const double*>(g), p->refinements, stream);
+  return solve_core(p, phi, g, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int poisfft_plan_set_refinements(poisfft_plan* p, int refinements) {
+  if (!p || p->dtype != POISFFT_MIXED || refinements < 0 || refinements > 8) return POISFFT_ERR_INVALID_ARG;
+  p->refinements = refinements;
+  return POISFFT_OK;
 }
 
 int poisfft_solve_strided(poisfft_plan* p, void* phi, const int64_t phi_ld[2], const void* g, const int64_t g_ld[2],
                           void* stream) {
   if (!p || !phi || !g || !phi_ld || !g_ld) return POISFFT_ERR_INVALID_ARG;
+  if (p->dtype == POISFFT_MIXED) return POISFFT_ERR_NOT_IMPLEMENTED;
   if (((uintptr_t)phi % p->esize) != 0 || ((uintptr_t)g % p->esize) != 0) return POISFFT_ERR_MISALIGNED;
   const long long nx = p->nx, ny = p->ny;
   const long long gy = p->dims >= 2 ? g_ld[0] : nx, pyy = p->dims >= 2 ? phi_ld[0] : nx;
@@ -980,17 +1039,18 @@ int poisfft_solve_strided(poisfft_plan* p, void* phi, const int64_t phi_ld[2], c
 int poisfft_solve_host(poisfft_plan* p, void* phi_host, const void* g_host, void* stream) {
   if (!p || !phi_host || !g_host) return POISFFT_ERR_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t fb = user_field_bytes(p);
   if (!p->stage_g) {
-    if (cudaMalloc(&p->stage_g, p->field_bytes) != cudaSuccess) { cudaGetLastError(); p->stage_g = nullptr; return POISFFT_ERR_ALLOC; }
+    if (cudaMalloc(&p->stage_g, fb) != cudaSuccess) { cudaGetLastError(); p->stage_g = nullptr; return POISFFT_ERR_ALLOC; }
   }
   if (!p->stage_phi) {
-    if (cudaMalloc(&p->stage_phi, p->field_bytes) != cudaSuccess) { cudaGetLastError(); p->stage_phi = nullptr; return POISFFT_ERR_ALLOC; }
+    if (cudaMalloc(&p->stage_phi, fb) != cudaSuccess) { cudaGetLastError(); p->stage_phi = nullptr; return POISFFT_ERR_ALLOC; }
   }
-  if (cudaMemcpyAsync(p->stage_g, g_host, p->field_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+  if (cudaMemcpyAsync(p->stage_g, g_host, fb, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return POISFFT_ERR_CUDA;
   int rc = poisfft_solve(p, p->stage_phi, p->stage_g, stream);
   if (rc != POISFFT_OK) return rc;
-  if (cudaMemcpyAsync(phi_host, p->stage_phi, p->field_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+  if (cudaMemcpyAsync(phi_host, p->stage_phi, fb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return POISFFT_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return POISFFT_ERR_CUDA;
   return POISFFT_OK;
@@ -1163,7 +1223,7 @@ extern "C" int poisfft_zero_mode_mean(poisfft_plan* p, const void* g, double* me
   if (!p || !g || !mean) return POISFFT_ERR_INVALID_ARG;
   if (!p->singular) return POISFFT_ERR_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  int rc = zero_mode_sum(p, g, p->esize == 8, st);
+  int rc = zero_mode_sum(p, g, p->esize == 8 || p->dtype == POISFFT_MIXED, st);
   if (rc != POISFFT_OK) return rc;
   double sum = 0.0;
   if (cudaMemcpyAsync(&sum, p->zm, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -1278,7 +1338,7 @@ __global__ void add_f32_kernel(double* __restrict__ phi, const float* __restrict
 extern "C" int poisfft_solve_refined(poisfft_plan* p, double* phi, const double* g, int refinements, void* stream) {
   if (!p || !phi || !g || refinements < 0 || refinements > 8 || (const void*)phi == (const void*)g)
     return POISFFT_ERR_INVALID_ARG;
-  if (p->dtype != POISFFT_F32 || p->approx != POISFFT_FD2) return POISFFT_ERR_INVALID_ARG;
+  if ((p->dtype != POISFFT_F32 && p->dtype != POISFFT_MIXED) || p->approx != POISFFT_FD2) return POISFFT_ERR_INVALID_ARG;
   if ((uintptr_t)phi % 8 != 0 || (uintptr_t)g % 8 != 0) return POISFFT_ERR_MISALIGNED;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const long long N = (long long)p->nx * p->ny * p->nz;
@@ -1322,13 +1382,13 @@ extern "C" int poisfft_solve_refined(poisfft_plan* p, double* phi, const double*
   }
   to_f32_kernel<<<g1, 256, 0, st>>>(g, p->refine_r, N, zsum, inv_w);
   if (cudaGetLastError() != cudaSuccess) return POISFFT_ERR_CUDA;
-  rc = poisfft_solve(p, p->refine_r, p->refine_r, stream);
+  rc = solve_core(p, p->refine_r, p->refine_r, st);
   if (rc != POISFFT_OK) return rc;
   add_f32_kernel<<<g1, 256, 0, st>>>(phi, p->refine_r, N, 1);
   for (int k = 0; k < refinements; k++) {
     fd2_residual_kernel<<<gr, 256, 0, st>>>(phi, g, p->refine_r, A[0], A[1], A[2], w2, rows, zsum, inv_w);
     if (cudaGetLastError() != cudaSuccess) return POISFFT_ERR_CUDA;
-    rc = poisfft_solve(p, p->refine_r, p->refine_r, stream);
+    rc = solve_core(p, p->refine_r, p->refine_r, st);
     if (rc != POISFFT_OK) return rc;
     add_f32_kernel<<<g1, 256, 0, st>>>(phi, p->refine_r, N, 0);
   }
@@ -1422,75 +1482,38 @@ void release_noalloc_plan(poisfft_plan* p) {
 
 extern "C" int poisfft_solve_noalloc(int dims, const int64_t n[], const double L[], const int bc[], int approx,
                                      int dtype, void* phi, const void* g, void* stream) {
-  if (!n || !L || !bc || !phi || !g || dims < 1 || dims > 3) return POISFFT_ERR_INVALID_ARG;
-  if (approx != POISFFT_SPECTRAL && approx != POISFFT_FD2) return POISFFT_ERR_INVALID_ARG;
-  if (dtype != POISFFT_F32 && dtype != POISFFT_F64) return POISFFT_ERR_INVALID_ARG;
-  int bca[3] = {POISFFT_P, POISFFT_P, POISFFT_P};
-  long long nn[3] = {1, 1, 1};
-  double LL[3] = {1.0, 1.0, 1.0};
-  for (int a = 0; a < dims; a++) {
-    if (n[a] < 1 || n[a] > (1 << 24)) return POISFFT_ERR_INVALID_ARG;
-    if (!(L[a] > 0.0) || !isfinite(L[a])) return POISFFT_ERR_INVALID_ARG;
-    const int b0 = bc[2 * a], b1 = bc[2 * a + 1];
-    if (b0 < POISFFT_P || b0 > POISFFT_NS || b1 < POISFFT_P || b1 > POISFFT_NS) return POISFFT_ERR_INVALID_ARG;
-    if (b0 != b1) return POISFFT_ERR_UNSUPPORTED_BC;
-    if (b0 == POISFFT_NR && n[a] < 2) return POISFFT_ERR_INVALID_ARG;
-    bca[a] = b0;
-    nn[a] = n[a];
-    LL[a] = L[a];
-  }
+  if (!phi || !g) return POISFFT_ERR_INVALID_ARG;
+  PlanArgs args;
+  int rc = validate_args(dims, n, L, bc, approx, dtype, args);
+  if (rc != POISFFT_OK) return rc;
+  if (dtype == POISFFT_MIXED) return POISFFT_ERR_NOT_IMPLEMENTED;
   const size_t esize = dtype == POISFFT_F32 ? 4 : 8;
   if (((uintptr_t)phi % esize) != 0 || ((uintptr_t)g % esize) != 0) return POISFFT_ERR_MISALIGNED;
-  const bool xper = bca[0] == POISFFT_P;
+  const bool xper = args.bc[0] == POISFFT_P;
   bool any_per_yz = false;
-  for (int a = 1; a < dims; a++) any_per_yz |= bca[a] == POISFFT_P;
+  for (int a = 1; a < dims; a++) any_per_yz |= args.bc[a] == POISFFT_P;
   if (!xper && any_per_yz) return POISFFT_ERR_NOT_IMPLEMENTED;
   // workspace size before any host planning: reject what cannot fit
-  const long long ncols0 = xper ? nn[0] / 2 + 1 : (nn[0] + 1) / 2;
+  const long long ncols0 = xper ? args.n[0] / 2 + 1 : (args.n[0] + 1) / 2;
   const long long pitch0 = (ncols0 + 1) / 2 * 2;
-  const double ws_need = (double)pitch0 * 2 * esize * nn[1] * nn[2];
+  const double ws_need = (double)pitch0 * 2 * esize * args.n[1] * args.n[2];
   if (ws_need + 256 > (double)kNoAllocBytes) return POISFFT_ERR_UNSUPPORTED_SIZE;
+  // the table copies below read host vectors that live only during this call
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) { cudaGetLastError(); return POISFFT_ERR_CUDA; }
+  if (cap != cudaStreamCaptureStatusNone) return POISFFT_ERR_NOT_IMPLEMENTED;
 
   poisfft_plan* p = new (std::nothrow) poisfft_plan();
   if (!p) return POISFFT_ERR_ALLOC;
-  p->dims = dims;
-  p->dtype = dtype;
-  p->approx = approx;
-  p->nx = (int)nn[0];
-  p->ny = (int)nn[1];
-  p->nz = (int)nn[2];
-  p->esize = esize;
-  p->r2c = xper ? 1 : 0;
-  const int emax = dtype == POISFFT_F32 ? 40 : 16;
-  bool sing = true;
-  int rc = POISFFT_OK;
-  for (int a = 0; a < 3 && rc == POISFFT_OK; a++) {
-    const bool null_axis = a >= dims;
-    rc = build_axis(p->axes[a], bca[a], (int)nn[a], LL[a], approx, emax, null_axis);
-    if (!null_axis) sing = sing && (bca[a] == POISFFT_P || bca[a] == POISFFT_NR || bca[a] == POISFFT_NS);
-  }
-  if (rc != POISFFT_OK) { release_noalloc_plan(p); return rc; }
-  p->singular = sing ? 1 : 0;
-  p->ncols = (int)ncols0;
-  p->pitch = (int)pitch0;
-  p->ws_bytes = (size_t)p->pitch * 2 * p->esize * p->ny * p->nz;
-
-  std::vector<SweepLaunch> sw;
-  SweepLaunch Ls;
-  const int fused_axis = dims == 3 ? 2 : 1;
-  if ((rc = plan_x_sweep(p, 0, Ls)) == POISFFT_OK) sw.push_back(Ls);
-  if (rc == POISFFT_OK && dims == 3 && (rc = plan_strided_sweep(p, 1, 0, Ls)) == POISFFT_OK) sw.push_back(Ls);
-  if (rc == POISFFT_OK && (rc = plan_strided_sweep(p, fused_axis, 2, Ls)) == POISFFT_OK) sw.push_back(Ls);
-  if (rc == POISFFT_OK && dims == 3 && (rc = plan_strided_sweep(p, 1, 1, Ls)) == POISFFT_OK) sw.push_back(Ls);
-  if (rc == POISFFT_OK && (rc = plan_x_sweep(p, 1, Ls)) == POISFFT_OK) sw.push_back(Ls);
-  if (rc != POISFFT_OK) { release_noalloc_plan(p); return rc; }
-  p->sweeps = sw;
+  if ((rc = plan_host(p, args, true)) != POISFFT_OK) { release_noalloc_plan(p); return rc; }
+  for (const auto& Lw : p->sweeps)
+    if (Lw.kind != 0 && Lw.kind != 1) { release_noalloc_plan(p); return POISFFT_ERR_NOT_IMPLEMENTED; }
 
   // carve the scratch array: error flag | tables per axis | workspace
   void* scratch = nullptr;
   if ((rc = noalloc_scratch(&scratch)) != POISFFT_OK) { release_noalloc_plan(p); return rc; }
   unsigned char* base = static_cast<unsigned char*>(scratch);
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   size_t off = 0;
   p->err = reinterpret_cast<int*>(base);
   off = 256;
@@ -1504,27 +1527,24 @@ extern "C" int poisfft_solve_noalloc(int dims, const int64_t n[], const double L
     release_noalloc_plan(p);
     return POISFFT_ERR_CUDA;
   }
-  for (auto& Lw : p->sweeps) {
-    if (Lw.kind == 0) {
-      Lw.xa.tables = p->tables[0];
-      Lw.xa.perm = p->perm[0];
-      Lw.xa.ws = p->ws;
-      Lw.xa.err = p->err;
-    } else {
-      const int a = Lw.sa.axis_dim;
-      Lw.sa.tables = p->tables[a];
-      Lw.sa.perm = p->perm[a];
-      Lw.sa.data = p->ws;
-      Lw.sa.lam_in = p->lam[0];
-      Lw.sa.lam_ax = p->lam[a];
-      Lw.sa.lam_out = p->lam[a == 1 ? 2 : 1];
-      Lw.sa.err = p->err;
-    }
-  }
-  if ((rc = encode_maps(p)) == POISFFT_OK)
-    rc = esize == 4 ? enqueue<float>(p, phi, g, st) : enqueue<double>(p, phi, g, st);
+  patch_general(p);
+  if ((rc = encode_maps(p)) == POISFFT_OK) rc = solve_core(p, phi, g, st);
   release_noalloc_plan(p);
   return rc;
+}
+
+extern "C" int poisfft_noalloc_check(void* stream) {
+  void* scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc != POISFFT_OK) return rc;
+  if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return POISFFT_ERR_CUDA;
+  int h = 0;
+  if (cudaMemcpy(&h, scratch, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return POISFFT_ERR_CUDA;
+  if (h != 0) {
+    if (cudaMemset(scratch, 0, sizeof(int)) != cudaSuccess) return POISFFT_ERR_CUDA;
+    return POISFFT_ERR_TIMEOUT;
+  }
+  return POISFFT_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1723,6 +1743,7 @@ int poisfft_batch_create(poisfft_batch** out, int count, const int dims[], const
   if (!out) return POISFFT_ERR_INVALID_ARG;
   *out = nullptr;
   if (count < 1 || !dims || !n || !L || !bc) return POISFFT_ERR_INVALID_ARG;
+  if (dtype == POISFFT_MIXED) return POISFFT_ERR_NOT_IMPLEMENTED;
   poisfft_batch* b = new (std::nothrow) poisfft_batch();
   if (!b) return POISFFT_ERR_ALLOC;
   std::vector<double> load;

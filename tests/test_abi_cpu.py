@@ -56,6 +56,8 @@ def test_status_strings(pb):
     (((8, 8, 8), (1, 1, 1), (0, 0, 0, 0, 0, 3), 1, 0), -2),
     (((8, 8, 8), (1, 1, 1), (2, 0, 4), 1, 0), None),                 # x non-periodic with periodic y
     (((8, 8, 8), (1, 1, 1), (4, 4, 0), 1, 0), None),                 # x non-periodic with periodic z
+    (((8, 8, 8), (1, 1, 1), (0, 2, 4), 1, 2), None),                 # MIXED (FD2)
+    (((8, 8, 8), (1, 1, 1), (0, 2, 4), 0, 2), -8),                   # MIXED needs FD2 eigenvalues
 ])
 def test_plan_create_validation(pb, args, expect):
     rc, plan = pb.plan_create(*args)
@@ -85,3 +87,19 @@ def test_null_plan_calls(pb):
     assert pb.lib.poisfft_destroy(None) == pb.OK
     info = (ctypes.c_int64 * 4)()
     assert pb.lib.poisfft_plan_info(None, info) == pb.ERR_INVALID_ARG
+
+
+def test_mixed_dtype_host_checks(pb):
+    """MIXED is a plan dtype (Sec. 3: one solver object per precision); the
+    calls that do not implement it say so before any CUDA call."""
+    assert pb.MIXED == 2
+    assert pb.lib.poisfft_plan_set_refinements(None, 1) == pb.ERR_INVALID_ARG
+    g = ctypes.c_double()
+    rc = pb.solve_noalloc((8, 8), (1, 1), (pb.P, pb.NS), pb.FD2, pb.MIXED, ctypes.addressof(g), ctypes.addressof(g))
+    assert rc == pb.ERR_NOT_IMPLEMENTED
+    n = (ctypes.c_int64 * 3)(8, 8, 8)
+    L = (ctypes.c_double * 3)(1, 1, 1)
+    bc = (ctypes.c_int * 6)(*([0] * 6))
+    dims = (ctypes.c_int * 1)(3)
+    b = ctypes.c_void_p()
+    assert pb.lib.poisfft_batch_create(ctypes.byref(b), 1, dims, n, L, bc, 1, pb.MIXED) == pb.ERR_NOT_IMPLEMENTED

@@ -80,3 +80,38 @@ def test_refinement_argument_checks(pb):
         plan.solve_refined(phi, g, refinements=1)            # zero source: zero solution
         torch.cuda.synchronize()
         assert float(phi.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("n,bcs", [((24, 20, 18), (W.P, W.DS, W.NS)), ((64, 64, 128), (W.P, W.P, W.NS)),
+                                   ((16, 12, 10), (W.NR, W.NR, W.NR))], ids=lambda v: str(v))
+def test_mixed_dtype_plan_through_poisfft_solve(pb, n, bcs):
+    """A POISFFT_MIXED plan (Sec. 3: one solver object per precision) takes
+    float64 arrays through the plain poisfft_solve: FP32 transforms refined
+    with FP64 FD2 residuals, two steps by default, one after
+    poisfft_plan_set_refinements(1)."""
+    shape = tuple(reversed(n))
+    Ls = (1.0, 1.5, 2.0)
+    g = W.normal(shape, 23, dtype=np.float64)
+    ref = O.solve(g, bcs, Ls, O.FD2, method="fft")
+    gd = torch.from_numpy(g).cuda()
+    with pb.Plan(n, Ls, bcs, pb.FD2, pb.MIXED) as plan:
+        phi = torch.full_like(gd, float("nan"))
+        plan.solve(phi, gd, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert plan.check() == pb.OK
+        err2 = O.rel_max_error(phi.cpu().numpy(), ref)
+        plan.set_refinements(0)
+        phi0 = torch.full_like(gd, float("nan"))
+        plan.solve(phi0, gd, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        err0 = O.rel_max_error(phi0.cpu().numpy(), ref)
+        # host buffers of doubles through the same plan
+        ph = np.full(shape, np.nan)
+        plan.set_refinements(2)
+        plan.solve_host(ph, g)
+        errh = O.rel_max_error(ph, ref)
+        with pytest.raises(pb.PoisFFTError):
+            plan.solve(gd, gd)                                # in place is refused
+        with pytest.raises(pb.PoisFFTError):
+            plan.set_refinements(9)
+    assert err0 < 1e-5 and err2 < 1e-10 and errh < 1e-10, (err0, err2, errh)

@@ -1,8 +1,10 @@
 """poisfft_solve_noalloc: the solve for callers that cannot allocate device
 memory (frameworks that own the device memory through their own pool,
-plug-ins with a fixed footprint).  It must give the same result as the plan
-based poisfft_solve, call after call, although every call reuses the same
-fixed device array.  This file is collected last on purpose."""
+plug-ins with a fixed footprint).  Every call reuses the same fixed device
+array, so each result is checked, call after call, against the FP64 CPU
+oracle on the same input, and against the plan-based poisfft_solve; the
+error flag that poisfft_noalloc_check reads must be clear after each call.
+This file is collected last on purpose."""
 
 import numpy as np
 import pytest
@@ -34,25 +36,47 @@ def pb():
 
 
 @pytest.mark.parametrize("n,bcs,approx,dtype,tol", CASES)
-def test_noalloc_matches_plan_solve_twice(pb, n, bcs, approx, dtype, tol):
+def test_noalloc_matches_oracle_twice(pb, n, bcs, approx, dtype, tol):
     Ls = tuple(1.0 + 0.1 * a for a in range(len(n)))
     pdt = pb.F32 if dtype == "f32" else pb.F64
     tdt = torch.float32 if dtype == "f32" else torch.float64
     stream = torch.cuda.current_stream()
     with pb.Plan(n, Ls, bcs, approx, pdt) as plan:
         for call in range(2):
-            g = torch.from_numpy(W.normal(tuple(reversed(n)), 40 + call, dtype=np.float64)).to("cuda", tdt)
-            ref = torch.empty_like(g)
-            plan.solve(ref, g, stream)
+            g64 = W.normal(tuple(reversed(n)), 40 + call, dtype=np.float64)
+            g = torch.from_numpy(g64).to("cuda", tdt)
+            # the oracle sees exactly the values the GPU reads
+            oracle = O.solve(g.cpu().numpy().astype(np.float64), bcs, Ls, approx)
             out = torch.full_like(g, float("nan"))
             rc = pb.solve_noalloc(n, Ls, bcs, approx, pdt, out, g, stream)
             assert rc == pb.OK, pb.status_string(rc)
+            assert pb.noalloc_check(stream) == pb.OK
+            err = O.rel_max_error(out.cpu().numpy(), oracle)
+            assert err < tol, f"call {call}: rel err {err:.3e} vs the FP64 oracle"
+            ref = torch.empty_like(g)
+            plan.solve(ref, g, stream)
             torch.cuda.synchronize()
-            err = O.rel_max_error(out.cpu().numpy(), ref.cpu().numpy())
-            assert err < tol, f"call {call}: rel err {err:.3e} vs poisfft_solve"
+            err2 = O.rel_max_error(out.cpu().numpy(), ref.cpu().numpy())
+            assert err2 < tol, f"call {call}: rel err {err2:.3e} vs poisfft_solve"
 
 
 def test_noalloc_rejects_oversized_grid(pb):
     g = torch.zeros(1, device="cuda")
     rc = pb.solve_noalloc((512, 512, 512), (1, 1, 1), (W.P, W.P, W.NS), W.FD2, pb.F32, g, g, None)
     assert rc == pb.ERR_UNSUPPORTED_SIZE
+
+
+def test_noalloc_refuses_stream_capture(pb):
+    """Its table copies read host memory that does not outlive the call, so
+    a capturing stream gets NOT_IMPLEMENTED and nothing is recorded."""
+    n = (16, 12)
+    g = torch.zeros(n[1], n[0], device="cuda")
+    phi = torch.zeros_like(g)
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph, stream=s):
+        phi.mul_(1.0)  # keeps the captured graph non-empty
+        rc = pb.solve_noalloc(n, (1, 1), (W.P, W.NS), W.FD2, pb.F32, phi, g, s)
+    assert rc == pb.ERR_NOT_IMPLEMENTED
+    assert pb.noalloc_check(None) == pb.OK
