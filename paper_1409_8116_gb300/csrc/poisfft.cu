@@ -67,34 +67,44 @@ double sin_pi_frac(long long num, long long den) {  // sin(pi num/den)
 // ---------------------------------------------------------------------------
 constexpr int kBluesteinMinPrime = 41;  // larger prime factors go through Bluestein
 
-// In-place forward DFT (exp(-2 pi i jk/N)) of a power-of-two length, FP64,
-// iterative radix 2 with exactly reduced twiddles (host tables only).
-void host_fft_pow2(std::vector<double>& re, std::vector<double>& im) {
-  const int N = (int)re.size();
-  for (int i = 1, j = 0; i < N; i++) {
-    int bit = N >> 1;
-    for (; j & bit; bit >>= 1) j ^= bit;
-    j ^= bit;
-    if (i < j) {
-      std::swap(re[i], re[j]);
-      std::swap(im[i], im[j]);
-    }
+// Forward DFT (exp(-2 pi i jk/N)) of a {2,3,5,7}-smooth length N, FP64,
+// recursive mixed-radix decimation in time with exactly reduced twiddles
+// (host tables only): with p the smallest prime factor of N and m = N/p,
+// X[k + m q] = sum_r exp(-2 pi i r (k + m q) / N) Y_r[k], Y_r the length-m
+// DFT of the samples r, r + p, r + 2p, ...
+void host_fft_rec(const double* re, const double* im, long long stride, int N, double* ore, double* oim) {
+  if (N == 1) {
+    ore[0] = re[0];
+    oim[0] = im[0];
+    return;
   }
-  for (int len = 2; len <= N; len <<= 1) {
-    for (int k = 0; k < len / 2; k++) {
-      double s, c;
-      sincos_2pi_frac(k, len, &s, &c);
-      const double wr = c, wi = -s;
-      for (int i = k; i < N; i += len) {
-        const int j = i + len / 2;
-        const double tr = re[j] * wr - im[j] * wi, ti = re[j] * wi + im[j] * wr;
-        re[j] = re[i] - tr;
-        im[j] = im[i] - ti;
-        re[i] += tr;
-        im[i] += ti;
+  int p = 2;
+  while (N % p) p++;
+  const int m = N / p;
+  std::vector<double> yr((size_t)N), yi((size_t)N);
+  for (int r = 0; r < p; r++) host_fft_rec(re + r * stride, im + r * stride, stride * p, m, &yr[(size_t)r * m], &yi[(size_t)r * m]);
+  for (int k = 0; k < m; k++)
+    for (int q = 0; q < p; q++) {
+      const int kk = k + m * q;
+      double sr = 0.0, si = 0.0;
+      for (int r = 0; r < p; r++) {
+        double sn, c;
+        sincos_2pi_frac((long long)r * kk, N, &sn, &c);  // exp(-2 pi i r kk / N)
+        const double ar = yr[(size_t)r * m + k], ai = yi[(size_t)r * m + k];
+        sr += ar * c + ai * sn;
+        si += ai * c - ar * sn;
       }
+      ore[kk] = sr;
+      oim[kk] = si;
     }
-  }
+}
+
+void host_fft(std::vector<double>& re, std::vector<double>& im) {
+  const int N = (int)re.size();
+  std::vector<double> orr((size_t)N), oi((size_t)N);
+  host_fft_rec(re.data(), im.data(), 1, N, orr.data(), oi.data());
+  re.swap(orr);
+  im.swap(oi);
 }
 
 bool is_unrolled_radix(int r, int emax) {
@@ -121,6 +131,37 @@ void factor_passes(int M, int emax, std::vector<int>& radices) {
   for (int p = 11; (long long)p * p <= M; p += 2)
     while (M % p == 0) { radices.push_back(p); M /= p; }
   if (M > 1) radices.push_back(M);
+}
+
+bool smooth7(long long v) {
+  for (int p : {2, 3, 5, 7})
+    while (v % p == 0) v /= p;
+  return v == 1;
+}
+
+// Convolution length of Bluestein's method for a DFT of length M: at least
+// 2M - 1 and {2,3,5,7}-smooth, so that every pass is an unrolled radix.  Of
+// those up to the next power of two, the one with the least estimated work
+// (length x passes) is taken: e.g. M = 4098 (DST-I of 2048 points) takes
+// 8960 = 16 * 16 * 5 * 7 instead of 16384, and its column tile fits in shared
+// memory.
+int bluestein_length(int M, int emax) {
+  const long long lo = 2LL * M - 1;
+  long long p2 = 1;
+  while (p2 < lo) p2 *= 2;
+  std::vector<int> rad;
+  factor_passes((int)p2, emax, rad);
+  long long best = p2, best_cost = p2 * (long long)rad.size();
+  for (long long L = lo; L < p2; L++) {
+    if (!smooth7(L)) continue;
+    factor_passes((int)L, emax, rad);
+    const long long cost = L * (long long)rad.size();
+    if (cost < best_cost && (int)rad.size() <= kMaxPass) {
+      best = L;
+      best_cost = cost;
+    }
+  }
+  return (int)best;
 }
 
 struct AxisPlan {
@@ -168,8 +209,7 @@ int build_axis(AxisPlan& ax, int bc, int n, double L, int approx, int emax, bool
   const bool blu = maxp >= kBluesteinMinPrime;
   int Mfft = M;
   if (blu) {
-    Mfft = 1;
-    while (Mfft < 2 * M - 1) Mfft *= 2;
+    Mfft = bluestein_length(M, emax);
     factor_passes(Mfft, emax, radices);
   }
   d.blu = blu ? 1 : 0;
@@ -249,7 +289,7 @@ int build_axis(AxisPlan& ax, int bc, int n, double L, int approx, int emax, bool
         bi[Mfft - m] = ci[m];
       }
     }
-    host_fft_pow2(br, bi);
+    host_fft(br, bi);
     d.bhat_off = (int)ax.tab_re.size();
     std::vector<double> hr(Mfft), hi(Mfft);
     for (int k = 0; k < Mfft; k++) {
