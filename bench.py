@@ -399,6 +399,9 @@ def run_ours(args):
     mixed = None
     if rank == 0 and not args.no_mixed and not f64 and spec["approx"] == pb.FD2:
         mixed = mixed_form(pb, plan, spec, g_host, ref if err is not None else None, stream, args)
+    tcf = None
+    if rank == 0 and not args.no_mixed and not f64:
+        tcf = tensor_core_form(pb, spec, g, ref if err is not None else None, stream, args)
     if err is not None:
         del ref
     zero_mode = None
@@ -420,7 +423,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if f64 else "f32", "data": "synthetic",
             "config": workload_config(args.workload, spec),
             "max_rel_err_vs_fp64": err, "zero_mode": zero_mode, "cufft_comparison": cufft,
-            "mixed_precision": mixed,
+            "mixed_precision": mixed, "bf16x3_tensor_core": tcf,
             "hbm_frac_step": step_bytes * args.steps / (ms_max / 1e3) / 1e9 / peak,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -482,6 +485,49 @@ def mixed_form(pb, plan, spec, g_host, ref, stream, args):
     out["fp64_direct"] = {"ms_per_solve": ms64, "max_rel_err_vs_fp64": rel_err(phi64)}
     plan64.close()
     del g64, phi64, ref_d
+    torch.cuda.empty_cache()
+    return out
+
+
+def tensor_core_form(pb, spec, g, ref, stream, args):
+    """The same FP32 field solved by a POISFFT_BF16X3 plan: the DFT blocks of
+    the 1024-point strided axes as split-BF16 tensor-core GEMMs (tcgen05,
+    FP32 accumulation); time per solve, per-launch times and the error
+    against the FP64 oracle.  None when the plan has no such axis."""
+    import torch
+
+    try:
+        plan = pb.Plan(spec["n"], spec["Ls"], spec["bcs"], spec["approx"], pb.BF16X3)
+    except pb.PoisFFTError as e:
+        return {"unavailable": str(e)}
+    phi = torch.empty_like(g)
+    for _ in range(max(1, min(args.warmup, 3))):
+        plan.solve(phi, g, stream)
+    stream.synchronize()
+    steps = max(1, min(args.steps, 10))
+    plan.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        plan.solve(phi, g, stream)
+    e1.record(stream)
+    stream.synchronize()
+    plan.profile(False)
+    per, ns = plan.profile_read()
+    assert plan.check(stream) == pb.OK
+    launches = plan.launches()
+    out = {"what": "POISFFT_BF16X3 plan: radix-32 DFT blocks of the 1024-point strided axes as tcgen05 GEMMs "
+                   "with hi/lo bfloat16 operands (three products, FP32 accumulation); other sweeps FP32",
+           "ms_per_solve": e0.elapsed_time(e1) / steps,
+           "launches": [dict(kernel=l["kernel"], mode=l["mode"], axis=l["axis"], ms=per[i] / ns)
+                        for i, l in enumerate(launches)],
+           "max_rel_err_vs_fp64": None}
+    if ref is not None:
+        ref_d = torch.from_numpy(ref).to("cuda")
+        out["max_rel_err_vs_fp64"] = float((phi.double() - ref_d).abs().max()) / float(ref_d.abs().max())
+        del ref_d
+    plan.close()
+    del phi
     torch.cuda.empty_cache()
     return out
 

@@ -44,8 +44,17 @@ typedef enum { POISFFT_SPECTRAL = 0, POISFFT_FD2 = 1 } poisfft_approx;
  * kernels) and the result is refined with residuals of the FD2 operator
  * (Eq. FD2-Laplace) formed in FP64, so the answer reaches the F64 solve's
  * accuracy class at a fraction of its cost (see poisfft_solve_refined, which
- * a MIXED plan's poisfft_solve runs).  MIXED needs approx POISFFT_FD2. */
-typedef enum { POISFFT_F32 = 0, POISFFT_F64 = 1, POISFFT_MIXED = 2 } poisfft_dtype;
+ * a MIXED plan's poisfft_solve runs).  MIXED needs approx POISFFT_FD2.
+ * BF16X3: float arrays; the radix-32 DFT blocks of 1024-point strided (y,
+ * z) axes run on the tensor cores (tcgen05) as GEMMs with operands split
+ * into two bfloat16 parts each and three products accumulated in FP32
+ * (hi*hi + lo*hi + hi*lo); everything else as F32.  About 2^-17 relative
+ * error per GEMM pass instead of 2^-24; plans need a strided axis of 1024
+ * points with the specialised FP32 kernels (otherwise
+ * POISFFT_ERR_NOT_IMPLEMENTED).  The forward and backward sweeps of a
+ * periodic axis and the fused divide sweep of a periodic, Neumann- or
+ * Dirichlet-staggered axis use it. */
+typedef enum { POISFFT_F32 = 0, POISFFT_F64 = 1, POISFFT_MIXED = 2, POISFFT_BF16X3 = 3 } poisfft_dtype;
 
 /* Status codes. */
 enum {
@@ -171,7 +180,7 @@ int poisfft_plan_info(const poisfft_plan* plan, int64_t info[4]);
  *     read host memory that does not outlive the call, so while `stream`
  *     is being captured the call returns POISFFT_ERR_NOT_IMPLEMENTED and
  *     enqueues nothing.
- * x non-periodic together with a periodic y or z, and dtype MIXED, return
+ * x non-periodic together with a periodic y or z, and dtypes MIXED and BF16X3, return
  * POISFFT_ERR_NOT_IMPLEMENTED here (poisfft_solve handles them).
  * Returns the status codes of poisfft_plan_create / poisfft_solve.  A
  * bounded device wait that gives up does not make the stream fail: it sets
@@ -217,7 +226,7 @@ int poisfft_plan_autotune(poisfft_plan* plan, void* stream);
 /* ---- Batched solves (many independent problems; no paper counterpart) ----
  * poisfft_batch_create: one plan per problem i with dims[i], n[3i..3i+2],
  *   L[3i..3i+2], bc[6i..6i+5] (entries beyond dims[i] ignored), a shared
- *   approx and dtype (F32 or F64; MIXED returns NOT_IMPLEMENTED), with the
+ *   approx and dtype (F32 or F64; MIXED and BF16X3 return NOT_IMPLEMENTED), with the
  *   default tile shapes (poisfft_batch_autotune tunes them in the batch's
  *   own setting).  Fails with the first failing plan's status.
  * poisfft_batch_solve: solves every problem (phi[i], g[i] as in
@@ -383,7 +392,8 @@ int poisfft_profile_read(poisfft_plan* plan, double* ms, int cap, int* nlaunch, 
 /* Description of launch position i of a solve (host only).
  *   out[0] = algorithmic HBM bytes of the launch (reads + writes of its data)
  *   out[1] = kernel: 0 contiguous (x) sweep, 1 strided (y/z) sweep,
- *            2 separate eigenvalue divide (x non-periodic with periodic y/z)
+ *            2 separate eigenvalue divide (x non-periodic with periodic y/z),
+ *            3 strided sweep on the tensor cores (BF16X3 plans)
  *   out[2] = mode: 0 forward, 1 backward, 2 forward + divide + backward
  *   out[3] = axis: 0 x, 1 y, 2 z
  * Returns POISFFT_OK or POISFFT_ERR_INVALID_ARG (i out of range). */

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libpoisfft.so")
 P, DR, DS, NR, NS = 0, 1, 2, 3, 4
 PCG_F64, PCG_MIXED = 0, 1
 SPECTRAL, FD2 = 0, 1
-F32, F64, MIXED = 0, 1, 2
+F32, F64, MIXED, BF16X3 = 0, 1, 2, 3
 
 OK = 0
 ERR_INVALID_ARG = -1
@@ -337,7 +337,7 @@ class Plan:
             rc = lib.poisfft_launch_info(self._p, i, v)
             if rc != OK:
                 raise PoisFFTError(rc, "poisfft_launch_info")
-            out.append(dict(bytes=v[0], kernel=("x_sweep", "strided_sweep", "pair_divide")[v[1]],
+            out.append(dict(bytes=v[0], kernel=("x_sweep", "strided_sweep", "pair_divide", "tc_strided_sweep")[v[1]],
                             mode=("forward", "backward", "fused")[v[2]], axis="xyz"[v[3]]))
         return out
 

@@ -11,6 +11,9 @@ namespace fast {
 struct FastStridedArgs;
 struct FastXArgs;
 }  // namespace fast
+namespace tc {
+struct TcStridedArgs;
+}  // namespace tc
 }  // namespace pf
 
 namespace pf {
@@ -32,5 +35,15 @@ cudaError_t launch_fast_strided(int M, int W, int mode, int kind, const CUtensor
                                 const fast::FastStridedArgs& a, unsigned grid, size_t smem, cudaStream_t s);
 cudaError_t launch_fast_x(int M, int mode, int kx, const fast::FastXArgs& a, unsigned grid, size_t smem,
                           cudaStream_t s);
+
+// Tensor-core sweeps of 1024-point strided axes (tc_f32.cu): mode and kind
+// as for launch_fast_strided (FM_FWD / FM_INV with FK_DFT; FM_FUSED with
+// FK_DFT or FK_DCT); persistent grid, fixed block and shared memory.
+cudaError_t launch_tc_strided(int mode, int kind, const CUtensorMap& map, const tc::TcStridedArgs& a, unsigned grid,
+                              cudaStream_t s);
+size_t tc_smem_bytes();
+// The four B operands F_hi, F_lo, G_hi, G_lo of the tensor-core sweeps as
+// bf16 bit patterns in their shared-memory layout (tc_f32.cu, host only).
+void tc_build_bmat(uint16_t* out);
 
 }  // namespace pf

@@ -23,6 +23,7 @@
 
 #include "../../include/poisfft.h"
 #include "fast_kernels.cuh"
+#include "tc_kernels.cuh"
 #include "reduce.cuh"
 #include "internal.h"
 #include "launch.h"
@@ -351,6 +352,8 @@ struct SweepLaunch {
   fast::FastStridedArgs fsa;
   PairDivideArgs pda;
   int M, fmode, fkind, axis, w, box_h;  // fast sweeps
+  int tc;                 // fast strided sweep on the tensor cores (BF16X3 plans)
+  int tc_tiles;           // its tiles (the persistent grid loops over them)
   int map;                // tensor map index (strided)
   unsigned grid;
   size_t smem;
@@ -424,6 +427,7 @@ struct poisfft_plan {
   void* fmk[3] = {nullptr, nullptr, nullptr};
   void* fpk[3] = {nullptr, nullptr, nullptr};
   void* flam[3] = {nullptr, nullptr, nullptr};
+  void* tcb = nullptr;               // B operands of the tensor-core sweeps (BF16X3 plans)
 };
 
 namespace {
@@ -449,6 +453,7 @@ void free_plan(poisfft_plan* p) {
     if (p->fpk[i]) cudaFree(p->fpk[i]);
     if (p->flam[i]) cudaFree(p->flam[i]);
   }
+  if (p->tcb) cudaFree(p->tcb);
   delete p;
 }
 
@@ -810,6 +815,12 @@ int enqueue(poisfft_plan* p, void* phi, const void* g, cudaStream_t st, const Fi
       a.phi_sy = fs.phi_sy;
       a.phi_sz = fs.phi_sz;
       e = launch_fast_x(L.M, L.fmode, L.fkind, a, L.grid, L.smem, st);
+    } else if (L.tc) {
+      tc::TcStridedArgs ta;
+      ta.f = L.fsa;
+      ta.bmat = static_cast<const uint4*>(p->tcb);
+      ta.ntiles = L.tc_tiles;
+      e = launch_tc_strided(L.fmode, L.fkind, p->maps[L.map], ta, L.grid, st);
     } else {
       e = launch_fast_strided(L.M, L.w, L.fmode, L.fkind, p->maps[L.map], L.fsa, L.grid, L.smem, st);
     }
@@ -842,7 +853,8 @@ int validate_args(int dims, const int64_t n[], const double L[], const int bc[],
                   PlanArgs& a) {
   if (!n || !L || !bc || dims < 1 || dims > 3) return POISFFT_ERR_INVALID_ARG;
   if (approx != POISFFT_SPECTRAL && approx != POISFFT_FD2) return POISFFT_ERR_INVALID_ARG;
-  if (dtype != POISFFT_F32 && dtype != POISFFT_F64 && dtype != POISFFT_MIXED) return POISFFT_ERR_INVALID_ARG;
+  if (dtype != POISFFT_F32 && dtype != POISFFT_F64 && dtype != POISFFT_MIXED && dtype != POISFFT_BF16X3)
+    return POISFFT_ERR_INVALID_ARG;
   a.dims = dims;
   a.approx = approx;
   a.dtype = dtype;
@@ -963,6 +975,21 @@ int plan_host(poisfft_plan* p, const PlanArgs& a, bool general_only) {
     sw.push_back(Ls);
   }
   p->sweeps = sw;
+  if (a.dtype == POISFFT_BF16X3) {
+    // the tensor-core sweeps take 1024-point strided axes: DFT forward and
+    // backward sweeps, and the fused sweep of a DFT or DCT-II/DST-II axis
+    int ntc = 0;
+    for (auto& L : p->sweeps) {
+      if (L.kind != 3 || L.M != tc::kM || L.w != tc::kW) continue;
+      const bool ok = (L.fmode == fast::FM_FUSED && (L.fkind == fast::FK_DFT || L.fkind == fast::FK_DCT)) ||
+                      (L.fmode != fast::FM_FUSED && L.fkind == fast::FK_DFT);
+      if (!ok) continue;
+      L.tc = 1;
+      L.tc_tiles = (int)L.grid;
+      ntc++;
+    }
+    if (ntc == 0) return POISFFT_ERR_NOT_IMPLEMENTED;
+  }
   return POISFFT_OK;
 }
 
@@ -991,6 +1018,21 @@ void patch_general(poisfft_plan* p) {
       L.sa.err = p->err;
     }
   }
+}
+
+// Tensor-core sweeps: upload the DFT-matrix operands and size the
+// persistent grids (two CTAs per SM).
+int tc_setup(poisfft_plan* p) {
+  std::vector<uint16_t> b(tc::kBmatBytes / 2);
+  tc_build_bmat(b.data());
+  if (cudaMalloc(&p->tcb, tc::kBmatBytes) != cudaSuccess) return POISFFT_ERR_ALLOC;
+  if (cudaMemcpy(p->tcb, b.data(), tc::kBmatBytes, cudaMemcpyHostToDevice) != cudaSuccess) return POISFFT_ERR_CUDA;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return POISFFT_ERR_CUDA;
+  for (auto& L : p->sweeps)
+    if (L.tc) L.grid = (unsigned)std::min<long long>(L.tc_tiles, 2LL * sms);
+  return POISFFT_OK;
 }
 
 // The FFT solve of the plan's kernels on arrays of its kernel precision.
@@ -1044,6 +1086,8 @@ int poisfft_plan_create(poisfft_plan** out, int dims, const int64_t n[], const d
   if (rc != POISFFT_OK) { cudaGetLastError(); free_plan(p); return rc; }
   if (p->fast) patch_fast(p);
   patch_general(p);
+  if (rc == POISFFT_OK && p->dtype == POISFFT_BF16X3) rc = tc_setup(p);
+  if (rc != POISFFT_OK) { cudaGetLastError(); free_plan(p); return rc; }
   if ((rc = encode_maps(p)) != POISFFT_OK) { free_plan(p); return rc; }
   *out = p;
   return POISFFT_OK;
@@ -1148,7 +1192,7 @@ int poisfft_launch_info(const poisfft_plan* p, int i, int64_t out[4]) {
   if (!p || !out || i < 0 || i >= (int)p->sweeps.size()) return POISFFT_ERR_INVALID_ARG;
   const SweepLaunch& L = p->sweeps[i];
   out[0] = L.bytes;
-  out[1] = (L.kind == 0 || L.kind == 2) ? 0 : (L.kind == 4 ? 2 : 1);
+  out[1] = (L.kind == 0 || L.kind == 2) ? 0 : (L.kind == 4 ? 2 : (L.tc ? 3 : 1));
   if (L.kind == 4) {
     out[2] = 2;
     out[3] = 0;
@@ -1526,7 +1570,7 @@ extern "C" int poisfft_solve_noalloc(int dims, const int64_t n[], const double L
   PlanArgs args;
   int rc = validate_args(dims, n, L, bc, approx, dtype, args);
   if (rc != POISFFT_OK) return rc;
-  if (dtype == POISFFT_MIXED) return POISFFT_ERR_NOT_IMPLEMENTED;
+  if (dtype == POISFFT_MIXED || dtype == POISFFT_BF16X3) return POISFFT_ERR_NOT_IMPLEMENTED;
   const size_t esize = dtype == POISFFT_F32 ? 4 : 8;
   if (((uintptr_t)phi % esize) != 0 || ((uintptr_t)g % esize) != 0) return POISFFT_ERR_MISALIGNED;
   const bool xper = args.bc[0] == POISFFT_P;
@@ -1783,7 +1827,7 @@ int poisfft_batch_create(poisfft_batch** out, int count, const int dims[], const
   if (!out) return POISFFT_ERR_INVALID_ARG;
   *out = nullptr;
   if (count < 1 || !dims || !n || !L || !bc) return POISFFT_ERR_INVALID_ARG;
-  if (dtype == POISFFT_MIXED) return POISFFT_ERR_NOT_IMPLEMENTED;
+  if (dtype == POISFFT_MIXED || dtype == POISFFT_BF16X3) return POISFFT_ERR_NOT_IMPLEMENTED;
   poisfft_batch* b = new (std::nothrow) poisfft_batch();
   if (!b) return POISFFT_ERR_ALLOC;
   std::vector<double> load;

@@ -103,3 +103,17 @@ def test_mixed_dtype_host_checks(pb):
     dims = (ctypes.c_int * 1)(3)
     b = ctypes.c_void_p()
     assert pb.lib.poisfft_batch_create(ctypes.byref(b), 1, dims, n, L, bc, 1, pb.MIXED) == pb.ERR_NOT_IMPLEMENTED
+
+
+def test_bf16x3_needs_a_1024_point_strided_axis(pb):
+    """The tensor-core form serves 1024-point strided axes; plans without
+    one are refused at planning time, before any CUDA call."""
+    assert pb.BF16X3 == 3
+    for n, bc in [((64, 64, 64), (0, 0, 0)), ((1024, 64, 64), (0, 0, 4)), ((100, 1024, 1024), (0, 0, 4)),
+                  ((1024, 1024), (4, 4))]:
+        rc, plan = pb.plan_create(n, (1,) * len(n), bc, 1, pb.BF16X3)
+        assert rc == pb.ERR_NOT_IMPLEMENTED, (n, bc, rc)
+    rc, plan = pb.plan_create((64, 64, 1024), (1, 1, 1), (0, 0, 4), 1, pb.BF16X3)
+    assert rc in (pb.OK, pb.ERR_CUDA)
+    if rc == pb.OK:
+        pb.destroy(plan)
