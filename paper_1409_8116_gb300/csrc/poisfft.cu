@@ -354,6 +354,7 @@ struct SweepLaunch {
   int M, fmode, fkind, axis, w, box_h;  // fast sweeps
   int tc;                 // fast strided sweep on the tensor cores (BF16X3 plans)
   int tc_tiles;           // its tiles (the persistent grid loops over them)
+  int tc_slot;            // its tile counter in poisfft_plan::tc_ctr
   int map;                // tensor map index (strided)
   unsigned grid;
   size_t smem;
@@ -428,6 +429,7 @@ struct poisfft_plan {
   void* fpk[3] = {nullptr, nullptr, nullptr};
   void* flam[3] = {nullptr, nullptr, nullptr};
   void* tcb = nullptr;               // B operands of the tensor-core sweeps (BF16X3 plans)
+  int* tc_ctr = nullptr;             // one tile counter per tensor-core launch
 };
 
 namespace {
@@ -454,6 +456,7 @@ void free_plan(poisfft_plan* p) {
     if (p->flam[i]) cudaFree(p->flam[i]);
   }
   if (p->tcb) cudaFree(p->tcb);
+  if (p->tc_ctr) cudaFree(p->tc_ctr);
   delete p;
 }
 
@@ -820,7 +823,9 @@ int enqueue(poisfft_plan* p, void* phi, const void* g, cudaStream_t st, const Fi
       ta.f = L.fsa;
       ta.bmat = static_cast<const uint4*>(p->tcb);
       ta.ntiles = L.tc_tiles;
-      e = launch_tc_strided(L.fmode, L.fkind, p->maps[L.map], ta, L.grid, st);
+      ta.counter = p->tc_ctr + L.tc_slot;
+      e = cudaMemsetAsync(ta.counter, 0, sizeof(int), st);
+      if (e == cudaSuccess) e = launch_tc_strided(L.fmode, L.fkind, p->maps[L.map], ta, L.grid, st);
     } else {
       e = launch_fast_strided(L.M, L.w, L.fmode, L.fkind, p->maps[L.map], L.fsa, L.grid, L.smem, st);
     }
@@ -1030,8 +1035,13 @@ int tc_setup(poisfft_plan* p) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return POISFFT_ERR_CUDA;
+  int slots = 0;
   for (auto& L : p->sweeps)
-    if (L.tc) L.grid = (unsigned)std::min<long long>(L.tc_tiles, 2LL * sms);
+    if (L.tc) {
+      L.grid = (unsigned)std::min<long long>(L.tc_tiles, 2LL * sms);
+      L.tc_slot = slots++;
+    }
+  if (cudaMalloc(&p->tc_ctr, (size_t)slots * sizeof(int)) != cudaSuccess) return POISFFT_ERR_ALLOC;
   return POISFFT_OK;
 }
 

@@ -59,6 +59,7 @@ struct TcStridedArgs {
   fast::FastStridedArgs f;  // tables, eigenvalues, layout (the FP32 kernel's)
   const uint4* bmat;        // F_hi | F_lo | G_hi | G_lo, canonical K-major (kBmatBytes)
   int ntiles;               // ntile_c * number of outer rows
+  int* counter;             // next tile to take (zero before the launch)
 };
 
 // ---------------------------------------------------------------------------
@@ -215,6 +216,7 @@ __global__ void __launch_bounds__(kThreadsTc, 2)
   float2* tws = reinterpret_cast<float2*>(Bm + kBmatBytes);
   uint64_t* bars = reinterpret_cast<uint64_t*>(Bm + kBmatBytes + kTwBytes);  // [0] TMA, [1] MMA
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2);
+  int* s_next = reinterpret_cast<int*>(bars + 3);  // the tile thread 0 took last
 
   const int tid = threadIdx.x, warp = tid >> 5;
   // GEMM row of this thread: 128 h + 32 (warp % 4) + lane (tensor-memory
@@ -276,10 +278,21 @@ __global__ void __launch_bounds__(kThreadsTc, 2)
     mma_pending = true;
   };
 
-  int tile = blockIdx.x;
-  if (tid == 0 && tile < A.ntiles) issue_tma(tile);
-  tma_pending = tile < A.ntiles;
-  for (; tile < A.ntiles; tile += gridDim.x) {
+  // Tiles are taken from a global counter in order, so the tiles in flight
+  // stay contiguous in memory (statically strided persistent CTAs drift
+  // apart and lose DRAM page locality).  Thread 0 takes the next tile and
+  // starts its load as soon as the shared tile is free; the others read
+  // its index after the end-of-tile barrier.  tma_pending is thread 0's.
+  auto take_next = [&]() {
+    const int nx = atomicAdd(A.counter, 1);
+    *s_next = nx;
+    tma_pending = nx < A.ntiles;
+    if (tma_pending) issue_tma(nx);
+  };
+  if (tid == 0) take_next();
+  __syncthreads();
+  int tile = *s_next;
+  while (tile < A.ntiles) {
     const bool ok = mbar_wait_bounded(&bars[0], tma_phase);
     tma_phase ^= 1;
     if (__syncthreads_or(!ok)) { bad = true; break; }
@@ -289,7 +302,6 @@ __global__ void __launch_bounds__(kThreadsTc, 2)
     const int col = c0 + c;
     const bool col_ok = col < a.ncols;
     float2* out = a.data + (size_t)outer * a.s_outer + c0 + c;
-    const int next = tile + gridDim.x;
     float2 v[kPer];  // indices i0 + i of this thread's row
 
     if (MODE == fast::FM_FWD || MODE == fast::FM_FUSED) {
@@ -309,14 +321,14 @@ __global__ void __launch_bounds__(kThreadsTc, 2)
       if (!wait_mma()) { bad = true; break; }
       tmem_row(tmem, h, part, v);  // row (s = hi3, c): X[s + 32 k2] in v[k2 - i0]
       if (MODE == fast::FM_FWD) {
-        if (tid == 0 && next < A.ntiles) issue_tma(next);
-        tma_pending = next < A.ntiles;
+        if (tid == 0) take_next();
         if (col_ok) {
 #pragma unroll
           for (int i = 0; i < kPer; i++) out[(size_t)(hi3 + 32 * (i0 + i)) * a.s_axis] = v[i];
         }
         tc_fence_before();
         __syncthreads();  // every row read before the next tile's pass 1 overwrites the accumulator
+        tile = *s_next;
         continue;
       }
       // ---- eigenvalue divide (and the DCT-II / DCT-III pair step)
@@ -374,8 +386,7 @@ __global__ void __launch_bounds__(kThreadsTc, 2)
     store_transposed(T, hi3, c, part, v);  // rows (a, c), K = s
     run_pass(bG, bGl);
     if (!wait_mma()) { bad = true; break; }
-    if (tid == 0 && next < A.ntiles) issue_tma(next);
-    tma_pending = next < A.ntiles;
+    if (tid == 0) take_next();
     tmem_row(tmem, h, part, v);  // row (a = hi3, c): x[a + 32 b] in v[b - i0]
     if (col_ok) {
 #pragma unroll
@@ -383,14 +394,15 @@ __global__ void __launch_bounds__(kThreadsTc, 2)
     }
     tc_fence_before();
     __syncthreads();
+    tile = *s_next;
   }
 
   // ---- clean-up: nothing of ours may be in flight when tensor memory is freed
   if (bad) {
     if (tid == 0) atomicExch(a.err, 1);
     // a wait flips its phase before it is checked: the pending one is the other
-    if (tma_pending) mbar_wait_bounded(&bars[0], tma_phase ^ 1);
-    if (mma_pending) mbar_wait_bounded(&bars[1], mma_phase ^ 1);
+    if (tid == 0 && tma_pending) mbar_wait_bounded(&bars[0], tma_phase ^ 1);
+    if (tid == 0 && mma_pending) mbar_wait_bounded(&bars[1], mma_phase ^ 1);
   }
   tc_fence_before();
   __syncthreads();
