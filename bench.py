@@ -81,6 +81,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer (e2e) measurement")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison")
+    ap.add_argument("--no-size256", action="store_true", help="skip the 256^3 line beside the 1024^3 one")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-precision (refined) and FP64 direct solves beside the FP32 one")
     return ap.parse_args()
@@ -412,9 +413,13 @@ def run_ours(args):
 
             zero_mode["mean_fp64_oracle"] = O.weighted_mean(g_host.astype(np.float64), spec["bcs"])
 
-    cpu = None
+    cpu = cpu_fft = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_sample_oracle(spec)
+        cpu_fft = cpu_fft_baseline(spec)
+    size256 = None
+    if rank == 0 and args.workload == DEFAULT_WORKLOAD and not args.no_size256:
+        size256 = size_256_line(pb, args, peak)
 
     if rank == 0:
         line = {
@@ -430,7 +435,7 @@ def run_ours(args):
                          "kernel": f"{launches[dom]['kernel']} ({launches[dom]['mode']}, axis {launches[dom]['axis']})",
                          "peak_source": f"{peak_kind} hbm_gbs"},
             "launches": per_launch,
-            "cpu_baseline": cpu,
+            "cpu_baseline": cpu, "cpu_fft_baseline": cpu_fft, "size_256": size256,
             "e2e": None if e2e_value is None else {
                 "value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": npts * esize,
                 "d2h_bytes_per_step": npts * esize,
@@ -485,6 +490,85 @@ def mixed_form(pb, plan, spec, g_host, ref, stream, args):
     out["fp64_direct"] = {"ms_per_solve": ms64, "max_rel_err_vs_fp64": rel_err(phi64)}
     plan64.close()
     del g64, phi64, ref_d
+    torch.cuda.empty_cache()
+    return out
+
+
+def cpu_fft_baseline(spec, n=256):
+    """The paper's method on the host cores: the FP64 oracle's scipy.fft
+    realisation of the Table 2 transforms (workers = every core), standing
+    in for the paper's FFTW build, on an n^3 sample with the workload's BCs."""
+    from oracle import poisson as O
+
+    g = W.normal((n, n, n), 98, dtype=np.float64)
+    O.solve(g, spec["bcs"], spec["Ls"], spec["approx"], method="fft")  # warm-up (plans, threads)
+    t0 = time.perf_counter()
+    reps = 2
+    for _ in range(reps):
+        O.solve(g, spec["bcs"], spec["Ls"], spec["approx"], method="fft")
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": n ** 3 / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "fft",
+            "sample": f"FP64 scipy.fft (pocketfft, workers = all cores) solve of a {n}^3 grid with the workload's "
+                      f"BCs {tuple(BC_NAME[b] for b in spec['bcs'])}; {dt:.2f} s per solve"}
+
+
+def size_256_line(pb, args, peak):
+    """The metric's second size, 256^3 (P, DS, NS), FD2, FP32: the field
+    (64 MiB) is smaller than L2, so a 512 MiB buffer is written between
+    timed solves; each solve is timed alone with CUDA events on its stream."""
+    import torch
+
+    name = "mixed_fd2_256_f32"
+    spec = W.WORKLOADS[name]
+    g_host = W.make_input(spec)
+    npts = int(np.prod(spec["n"]))
+    plan = pb.Plan(spec["n"], spec["Ls"], spec["bcs"], spec["approx"], pb.F32)
+    launches = plan.launches()
+    stream = torch.cuda.Stream()
+    g = torch.from_numpy(g_host).to("cuda")
+    phi = torch.empty_like(g)
+    flush = torch.empty(128 << 20, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            plan.solve(phi, g, stream)
+    steps = max(5, min(args.steps, 50))
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    plan.profile(True)
+    with torch.cuda.stream(stream):
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record(stream)
+            plan.solve(phi, g, stream)
+            e1.record(stream)
+    stream.synchronize()
+    plan.profile(False)
+    per, ns = plan.profile_read()
+    assert plan.check(stream) == pb.OK
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) / steps
+    dom = int(np.argmax(per))
+    dom_ms = per[dom] / ns
+    achieved = launches[dom]["bytes"] / (dom_ms / 1e3) / 1e9
+    step_bytes = sum(l["bytes"] for l in launches)
+    err = None
+    if not args.no_check:
+        from oracle import poisson as O
+
+        ref = O.solve(g_host.astype(np.float64), spec["bcs"], spec["Ls"], spec["approx"], method="fft")
+        err = O.rel_max_error(phi.cpu().numpy().astype(np.float64), ref)
+    out = {"config": workload_config(name, spec), "value": npts / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+           "steps": steps, "l2": "512 MiB written between timed solves (field smaller than L2)",
+           "hbm_frac_step": step_bytes / (ms / 1e3) / 1e9 / peak,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "kernel": f"{launches[dom]['kernel']} ({launches[dom]['mode']}, axis {launches[dom]['axis']})"},
+           "launches": [dict(kernel=l["kernel"], mode=l["mode"], axis=l["axis"], ms=per[i] / ns)
+                        for i, l in enumerate(launches)],
+           "max_rel_err_vs_fp64": err}
+    if not args.no_cufft:
+        out["cufft_comparison"] = cufft_comparison(g, args.warmup, min(args.steps, 10))
+    if not args.no_cpu_baseline:
+        out["cpu_fft_baseline"] = cpu_fft_baseline(spec)
+    plan.close()
+    del g, phi, flush
     torch.cuda.empty_cache()
     return out
 
@@ -574,6 +658,15 @@ def run_batch(args):
     for _ in range(args.warmup):
         batch.solve_sequential(phis, gs, stream)
     ms_plain = timed(batch.solve_sequential, args.steps)
+    # the plain form at its best: every plan's tiles tuned alone
+    plain_by_config = {}
+    for cand, cname in enumerate(pb.Batch.TUNE_CANDIDATES):
+        batch.select(cand)
+        for _ in range(max(1, args.warmup)):
+            batch.solve_sequential(phis, gs, stream)
+        plain_by_config[cname] = timed(batch.solve_sequential, args.steps) / args.steps
+    batch.select(chosen)
+    ms_plain_best = min(plain_by_config.values()) * args.steps
     assert batch.check(stream) == pb.OK
     value = throughput(npts, args.steps, 1, ms_graph / 1e3)
     err = None
@@ -583,7 +676,7 @@ def run_batch(args):
         batch.solve(phis, gs, stream)
         stream.synchronize()
         worst = 0.0
-        for p, g, phi in list(zip(probs, gs, phis))[:64]:
+        for p, g, phi in zip(probs, gs, phis):  # every problem of the batch
             ref = O.solve(g.cpu().numpy().astype(np.float64), p["bcs"], p["Ls"], spec["approx"], method="fft")
             worst = max(worst, O.rel_max_error(phi.cpu().numpy(), ref))
         err = worst
@@ -600,6 +693,37 @@ def run_batch(args):
                "kind": "oracle", "sample": "FP64 oracle (dense Table-1 matrices) on the 32 smallest problems of the "
                                            f"batch ({dt:.1f} s)"}
     peak, peak_kind = load_peaks()
+    info = batch.info()
+    achieved = info["bytes"] / (ms_graph / args.steps / 1e3) / 1e9
+    # end to end: pinned host inputs copied in, one graph replay, solutions
+    # copied back, every step
+    e2e = None
+    if not args.no_e2e:
+        gh = [x.cpu().pin_memory() for x in gs]
+        ph = [torch.empty_like(x).pin_memory() for x in gh]
+        gd2 = [torch.empty_like(x) for x in gs]
+        pd2 = [torch.empty_like(x) for x in gs]
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                for d, h in zip(gd2, gh):
+                    d.copy_(h, non_blocking=True)
+                batch.solve(pd2, gd2, stream)
+                for h, d in zip(ph, pd2):
+                    h.copy_(d, non_blocking=True)
+            stream.synchronize()
+
+        e2e_step()
+        e2e_steps = max(1, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        t_e2e = time.perf_counter() - t0
+        nbytes = sum(x.numel() * 4 for x in gs)
+        e2e = {"value": npts * e2e_steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes,
+               "path": "pinned host buffers, one copy per problem each way, batch graph replay in between"}
+        del gh, ph, gd2, pd2
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_graph / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -607,14 +731,16 @@ def run_batch(args):
         "config": {"workload": args.workload, "problems": len(probs), "points": npts,
                    "dims2": sum(p["dims"] == 2 for p in probs), "approx": "fd2",
                    "l2": "inputs larger than L2 (2.7 GB over the batch)"},
-        "plain_ms_per_step": ms_plain / args.steps, "speedup_vs_plain": ms_plain / ms_graph,
-        "create_s": t_create, "max_rel_err_vs_fp64_first64": err,
+        "plain_ms_per_step": ms_plain / args.steps, "plain_ms_per_step_by_config": plain_by_config,
+        "speedup_vs_best_plain": ms_plain_best / ms_graph, "speedup_vs_plain_same_tiles": ms_plain / ms_graph,
+        "create_s": t_create, "max_rel_err_vs_fp64": err, "checked_problems": None if err is None else len(probs),
         "autotune": {"kept": pb.Batch.TUNE_CANDIDATES[chosen],
                      "ms_per_replay": dict(zip(pb.Batch.TUNE_CANDIDATES, tune_ms)), "seconds": t_tune},
-        "roofline": {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None,
-                     "kernel": "batch graph (per-launch timing not available inside a graph)",
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "bytes_per_step": info["bytes"],
+                     "kernel": "whole batch graph: algorithmic bytes of every launch of every problem / replay time",
                      "peak_source": f"{peak_kind} hbm_gbs"},
-        "cpu_baseline": cpu, "e2e": None, "gpu_launches": None, "clocks": clocks,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": info["launches"] * args.steps, "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
     batch.close()

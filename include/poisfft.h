@@ -259,6 +259,17 @@ int poisfft_batch_solve_sequential(poisfft_batch* batch, void* const phi[], cons
 int poisfft_batch_autotune(poisfft_batch* batch, void* const phi[], const void* const g[], void* stream,
                            double ms[POISFFT_BATCH_TUNE_CANDIDATES], int* chosen);
 int poisfft_batch_check(poisfft_batch* batch, void* stream);
+/* poisfft_batch_info (host only): out[0] = algorithmic HBM bytes of one
+ * batch solve (reads + writes of every launch's data, summed over the
+ * problems), out[1] = kernel launches per batch solve, out[2] = grid points
+ * of all problems.  Returns POISFFT_OK or POISFFT_ERR_INVALID_ARG. */
+int poisfft_batch_info(const poisfft_batch* batch, int64_t out[3]);
+/* poisfft_batch_select: apply candidate configuration `candidate` (0..
+ * POISFFT_BATCH_TUNE_CANDIDATES-1) of the last poisfft_batch_autotune call,
+ * e.g. to time the plain form with every plan tuned alone.  The next
+ * poisfft_batch_solve re-captures the graph.  POISFFT_ERR_INVALID_ARG when
+ * no tuning has run or the candidate is out of range. */
+int poisfft_batch_select(poisfft_batch* batch, int candidate);
 int poisfft_batch_destroy(poisfft_batch* batch);
 
 /* ---- FFT-preconditioned CG for div(a grad phi) = g (Sec. 1: the fast solve

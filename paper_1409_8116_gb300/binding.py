@@ -53,6 +53,8 @@ EXPORTED = [
     "poisfft_batch_solve_sequential",
     "poisfft_batch_autotune",
     "poisfft_batch_check",
+    "poisfft_batch_info",
+    "poisfft_batch_select",
     "poisfft_batch_destroy",
     "poisfft_pcg_create",
     "poisfft_pcg_solve",
@@ -130,6 +132,10 @@ def _load():
                                          i64p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                                          ctypes.c_int, ctypes.c_int]
     lib.poisfft_batch_create.restype = ctypes.c_int
+    lib.poisfft_batch_info.argtypes = [ctypes.c_void_p, i64p]
+    lib.poisfft_batch_info.restype = ctypes.c_int
+    lib.poisfft_batch_select.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.poisfft_batch_select.restype = ctypes.c_int
     for nm in ("poisfft_batch_solve", "poisfft_batch_solve_sequential"):
         getattr(lib, nm).argtypes = [ctypes.c_void_p, vpp, vpp, ctypes.c_void_p]
         getattr(lib, nm).restype = ctypes.c_int
@@ -431,6 +437,20 @@ class Batch:
         if rc != OK:
             raise PoisFFTError(rc, "poisfft_batch_autotune")
         return chosen.value, list(ms)
+
+    def select(self, candidate):
+        """Apply one of the last autotune's candidate configurations."""
+        rc = lib.poisfft_batch_select(self._b, int(candidate))
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_batch_select")
+
+    def info(self):
+        """dict(bytes, launches, points) of one batch solve."""
+        out = (ctypes.c_int64 * 3)()
+        rc = lib.poisfft_batch_info(self._b, out)
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_batch_info")
+        return dict(bytes=out[0], launches=out[1], points=out[2])
 
     def check(self, stream=None):
         return lib.poisfft_batch_check(self._b, _stream(stream))

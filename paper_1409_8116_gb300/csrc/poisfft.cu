@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <nvtx3/nvToolsExt.h>
 #include <new>
 #include <vector>
 
@@ -32,6 +33,42 @@ using namespace pf;
 
 
 namespace {
+
+// ---------------------------------------------------------------------------
+// Host-side fault injection (a testing aid: nothing faults on the device).
+// POISFFT_FAULT is read when a call that allocates starts (plan creation,
+// host-buffer solve, refined solve, zero-mode mean, autotune):
+//   alloc:N  the N-th device allocation of that call (1-based) fails
+//   encode   encoding the TMA tensor maps fails (as cuTensorMapEncodeTiled would)
+//   size     planning reports an unsupported size
+// Every such failure must come back as its status code with nothing leaked.
+// ---------------------------------------------------------------------------
+struct FaultState {
+  int alloc_at = 0, alloc_seen = 0;
+  bool encode = false, size = false;
+};
+thread_local FaultState g_fault;
+
+struct FaultScope {  // armed for the duration of one API call
+  FaultScope() {
+    g_fault = FaultState();
+    const char* e = getenv("POISFFT_FAULT");
+    if (!e) return;
+    if (!strncmp(e, "alloc:", 6)) g_fault.alloc_at = atoi(e + 6);
+    else if (!strcmp(e, "encode")) g_fault.encode = true;
+    else if (!strcmp(e, "size")) g_fault.size = true;
+  }
+  ~FaultScope() { g_fault = FaultState(); }
+};
+
+template <typename T>
+cudaError_t dev_malloc(T** ptr, size_t bytes) {
+  if (g_fault.alloc_at > 0 && ++g_fault.alloc_seen == g_fault.alloc_at) {
+    *ptr = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(reinterpret_cast<void**>(ptr), bytes);
+}
 
 constexpr size_t kSmemLimit = 200 * 1024;   // dynamic smem budget of one CTA
 constexpr size_t kSmemTarget = 64 * 1024;   // preferred tile size (several CTAs per SM)
@@ -469,13 +506,13 @@ int upload_tables(poisfft_plan* p) {
     for (size_t i = 0; i < nt; i++) { tab[2 * i] = (T)ax.tab_re[i]; tab[2 * i + 1] = (T)ax.tab_im[i]; }
     std::vector<T> lam(ax.lam.size());
     for (size_t i = 0; i < lam.size(); i++) lam[i] = (T)ax.lam[i];
-    if (cudaMalloc(&p->tables[a], tab.size() * sizeof(T)) != cudaSuccess) return POISFFT_ERR_ALLOC;
-    if (cudaMalloc(&p->lam[a], std::max<size_t>(lam.size(), 1) * sizeof(T)) != cudaSuccess) return POISFFT_ERR_ALLOC;
+    if (dev_malloc(&p->tables[a], tab.size() * sizeof(T)) != cudaSuccess) return POISFFT_ERR_ALLOC;
+    if (dev_malloc(&p->lam[a], std::max<size_t>(lam.size(), 1) * sizeof(T)) != cudaSuccess) return POISFFT_ERR_ALLOC;
     if (cudaMemcpy(p->tables[a], tab.data(), tab.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
       return POISFFT_ERR_CUDA;
     if (cudaMemcpy(p->lam[a], lam.data(), lam.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
       return POISFFT_ERR_CUDA;
-    if (cudaMalloc(&p->perm[a], ax.perm.size() * sizeof(int)) != cudaSuccess) return POISFFT_ERR_ALLOC;
+    if (dev_malloc(&p->perm[a], ax.perm.size() * sizeof(int)) != cudaSuccess) return POISFFT_ERR_ALLOC;
     if (cudaMemcpy(p->perm[a], ax.perm.data(), ax.perm.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
       return POISFFT_ERR_CUDA;
   }
@@ -653,10 +690,10 @@ int fast_upload_axis(poisfft_plan* p, int a) {
     pk[4 * k] = lam[k];
     pk[4 * k + 1] = lam[k == 0 ? 0 : M - k];
   }
-  if (cudaMalloc(&p->ftw[a], tw.size() * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&p->fmk[a], mk.size() * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&p->fpk[a], pk.size() * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&p->flam[a], lam.size() * sizeof(float)) != cudaSuccess)
+  if (dev_malloc(&p->ftw[a], tw.size() * sizeof(float)) != cudaSuccess ||
+      dev_malloc(&p->fmk[a], mk.size() * sizeof(float)) != cudaSuccess ||
+      dev_malloc(&p->fpk[a], pk.size() * sizeof(float)) != cudaSuccess ||
+      dev_malloc(&p->flam[a], lam.size() * sizeof(float)) != cudaSuccess)
     return POISFFT_ERR_ALLOC;
   if (cudaMemcpy(p->ftw[a], tw.data(), tw.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(p->fmk[a], mk.data(), mk.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -752,6 +789,7 @@ void patch_fast(poisfft_plan* p) {
 }
 
 int encode_maps(poisfft_plan* p) {
+  if (g_fault.encode) return POISFFT_ERR_CUDA;
   EncodeTiledFn enc = get_encode_fn();
   if (!enc) return POISFFT_ERR_CUDA;
   const CUtensorMapDataType dt = p->esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
@@ -790,10 +828,31 @@ struct FieldStrides {
   long long g_sy, g_sz, phi_sy, phi_sz;
 };
 
+// NVTX range name of a launch (axis x mode; the separate divide)
+const char* sweep_range_name(const SweepLaunch& L) {
+  static const char* const names[3][3] = {
+      {"poisfft x forward", "poisfft x backward", "poisfft x fused"},
+      {"poisfft y forward", "poisfft y backward", "poisfft y fused"},
+      {"poisfft z forward", "poisfft z backward", "poisfft z fused"}};
+  if (L.kind == 4) return "poisfft eigenvalue divide";
+  const int axis = L.kind >= 2 ? L.axis : (L.kind == 0 ? 0 : L.sa.axis_dim);
+  const int mode = L.kind >= 2 ? L.fmode : (L.kind == 0 ? L.xa.mode : L.sa.mode);
+  return names[axis][mode];
+}
+
+// Ranges are pushed and popped around every launch of a solve (host side;
+// no cost beyond a pointer check when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 template <typename T>
 int enqueue(poisfft_plan* p, void* phi, const void* g, cudaStream_t st, const FieldStrides& fs) {
+  NvtxRange solve_range("poisfft solve");
   for (auto& L : p->sweeps) {
     if (p->profiling && record_event(p, st) != POISFFT_OK) return POISFFT_ERR_CUDA;
+    NvtxRange sweep_range(sweep_range_name(L));
     cudaError_t e;
     if (L.kind == 0) {
       XArgs a = L.xa;
@@ -887,6 +946,7 @@ int validate_args(int dims, const int64_t n[], const double L[], const int bc[],
 // non-periodic with a periodic y or z then returns
 // POISFFT_ERR_NOT_IMPLEMENTED.  No CUDA call.
 int plan_host(poisfft_plan* p, const PlanArgs& a, bool general_only) {
+  if (g_fault.size) return POISFFT_ERR_UNSUPPORTED_SIZE;
   const int dims = a.dims;
   // x periodic -> half-spectrum workspace; otherwise the real transformed
   // field viewed as complex pairs.  x non-periodic with a periodic y or z
@@ -1030,7 +1090,7 @@ void patch_general(poisfft_plan* p) {
 int tc_setup(poisfft_plan* p) {
   std::vector<uint16_t> b(tc::kBmatBytes / 2);
   tc_build_bmat(b.data());
-  if (cudaMalloc(&p->tcb, tc::kBmatBytes) != cudaSuccess) return POISFFT_ERR_ALLOC;
+  if (dev_malloc(&p->tcb, tc::kBmatBytes) != cudaSuccess) return POISFFT_ERR_ALLOC;
   if (cudaMemcpy(p->tcb, b.data(), tc::kBmatBytes, cudaMemcpyHostToDevice) != cudaSuccess) return POISFFT_ERR_CUDA;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -1041,7 +1101,7 @@ int tc_setup(poisfft_plan* p) {
       L.grid = (unsigned)std::min<long long>(L.tc_tiles, 2LL * sms);
       L.tc_slot = slots++;
     }
-  if (cudaMalloc(&p->tc_ctr, (size_t)slots * sizeof(int)) != cudaSuccess) return POISFFT_ERR_ALLOC;
+  if (dev_malloc(&p->tc_ctr, (size_t)slots * sizeof(int)) != cudaSuccess) return POISFFT_ERR_ALLOC;
   return POISFFT_OK;
 }
 
@@ -1079,6 +1139,7 @@ int poisfft_plan_create(poisfft_plan** out, int dims, const int64_t n[], const d
                         int approx, int dtype) {
   if (!out) return POISFFT_ERR_INVALID_ARG;
   *out = nullptr;
+  FaultScope fault;
   PlanArgs args;
   int rc = validate_args(dims, n, L, bc, approx, dtype, args);
   if (rc != POISFFT_OK) return rc;
@@ -1087,9 +1148,9 @@ int poisfft_plan_create(poisfft_plan** out, int dims, const int64_t n[], const d
   if ((rc = plan_host(p, args, false)) != POISFFT_OK) { free_plan(p); return rc; }
 
   // device resources
-  if (cudaMalloc(&p->err, sizeof(int)) != cudaSuccess) { cudaGetLastError(); free_plan(p); return POISFFT_ERR_CUDA; }
+  if (dev_malloc(&p->err, sizeof(int)) != cudaSuccess) { cudaGetLastError(); free_plan(p); return POISFFT_ERR_CUDA; }
   if (cudaMemset(p->err, 0, sizeof(int)) != cudaSuccess) { free_plan(p); return POISFFT_ERR_CUDA; }
-  if (cudaMalloc(&p->ws, p->ws_bytes) != cudaSuccess) { cudaGetLastError(); free_plan(p); return POISFFT_ERR_ALLOC; }
+  if (dev_malloc(&p->ws, p->ws_bytes) != cudaSuccess) { cudaGetLastError(); free_plan(p); return POISFFT_ERR_ALLOC; }
   if (cudaMemset(p->ws, 0, p->ws_bytes) != cudaSuccess) { free_plan(p); return POISFFT_ERR_CUDA; }
   rc = p->esize == 4 ? upload_tables<float>(p) : upload_tables<double>(p);
   for (int a = 0; p->fast && a < dims && rc == POISFFT_OK; a++) rc = fast_upload_axis(p, a);
@@ -1132,13 +1193,14 @@ int poisfft_solve_strided(poisfft_plan* p, void* phi, const int64_t phi_ld[2], c
 
 int poisfft_solve_host(poisfft_plan* p, void* phi_host, const void* g_host, void* stream) {
   if (!p || !phi_host || !g_host) return POISFFT_ERR_INVALID_ARG;
+  FaultScope fault;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t fb = user_field_bytes(p);
   if (!p->stage_g) {
-    if (cudaMalloc(&p->stage_g, fb) != cudaSuccess) { cudaGetLastError(); p->stage_g = nullptr; return POISFFT_ERR_ALLOC; }
+    if (dev_malloc(&p->stage_g, fb) != cudaSuccess) { cudaGetLastError(); p->stage_g = nullptr; return POISFFT_ERR_ALLOC; }
   }
   if (!p->stage_phi) {
-    if (cudaMalloc(&p->stage_phi, fb) != cudaSuccess) { cudaGetLastError(); p->stage_phi = nullptr; return POISFFT_ERR_ALLOC; }
+    if (dev_malloc(&p->stage_phi, fb) != cudaSuccess) { cudaGetLastError(); p->stage_phi = nullptr; return POISFFT_ERR_ALLOC; }
   }
   if (cudaMemcpyAsync(p->stage_g, g_host, fb, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return POISFFT_ERR_CUDA;
@@ -1284,8 +1346,8 @@ int zero_mode_sum(poisfft_plan* p, const void* g, bool f64, cudaStream_t st) {
     return POISFFT_ERR_CUDA;
   const unsigned nb = (unsigned)std::max<long long>(1, std::min<long long>((N + 255) / 256, (long long)sms * 8));
   if (!p->zm) {
-    if (cudaMalloc(&p->zm, (1 + (size_t)sms * 8) * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&p->zm_count, sizeof(unsigned)) != cudaSuccess ||
+    if (dev_malloc(&p->zm, (1 + (size_t)sms * 8) * sizeof(double)) != cudaSuccess ||
+        dev_malloc(&p->zm_count, sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(p->zm_count, 0, sizeof(unsigned)) != cudaSuccess) {
       cudaGetLastError();
       return POISFFT_ERR_ALLOC;
@@ -1316,6 +1378,7 @@ double zero_mode_weight(const poisfft_plan* p) {
 extern "C" int poisfft_zero_mode_mean(poisfft_plan* p, const void* g, double* mean, void* stream) {
   if (!p || !g || !mean) return POISFFT_ERR_INVALID_ARG;
   if (!p->singular) return POISFFT_ERR_INVALID_ARG;
+  FaultScope fault;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   int rc = zero_mode_sum(p, g, p->esize == 8 || p->dtype == POISFFT_MIXED, st);
   if (rc != POISFFT_OK) return rc;
@@ -1434,9 +1497,10 @@ extern "C" int poisfft_solve_refined(poisfft_plan* p, double* phi, const double*
     return POISFFT_ERR_INVALID_ARG;
   if ((p->dtype != POISFFT_F32 && p->dtype != POISFFT_MIXED) || p->approx != POISFFT_FD2) return POISFFT_ERR_INVALID_ARG;
   if ((uintptr_t)phi % 8 != 0 || (uintptr_t)g % 8 != 0) return POISFFT_ERR_MISALIGNED;
+  FaultScope fault;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const long long N = (long long)p->nx * p->ny * p->nz;
-  if (!p->refine_r && cudaMalloc(&p->refine_r, (size_t)N * sizeof(float)) != cudaSuccess) {
+  if (!p->refine_r && dev_malloc(&p->refine_r, (size_t)N * sizeof(float)) != cudaSuccess) {
     cudaGetLastError();
     p->refine_r = nullptr;
     return POISFFT_ERR_ALLOC;
@@ -1702,7 +1766,7 @@ int autotune_plan(poisfft_plan* p, cudaStream_t st) {
   void* phi = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = POISFFT_OK;
-  if (cudaMalloc(&g, p->field_bytes) != cudaSuccess || cudaMalloc(&phi, p->field_bytes) != cudaSuccess ||
+  if (dev_malloc(&g, p->field_bytes) != cudaSuccess || dev_malloc(&phi, p->field_bytes) != cudaSuccess ||
       cudaMemsetAsync(g, 0, p->field_bytes, st) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
       cudaEventCreate(&e1) != cudaSuccess)
     rc = POISFFT_ERR_ALLOC;
@@ -1751,6 +1815,7 @@ int autotune_plan(poisfft_plan* p, cudaStream_t st) {
 
 extern "C" int poisfft_plan_autotune(poisfft_plan* p, void* stream) {
   if (!p) return POISFFT_ERR_INVALID_ARG;
+  FaultScope fault;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   return p->esize == 4 ? autotune_plan<float>(p, st) : autotune_plan<double>(p, st);
 }
@@ -1773,6 +1838,7 @@ struct poisfft_batch {
   std::vector<const void*> g_cached;
   std::vector<void*> phi_cached;
   cudaStream_t stream_cached = nullptr;
+  std::vector<std::vector<SweepLaunch>> tuned[POISFFT_BATCH_TUNE_CANDIDATES];  // the last tuner's candidates
 };
 
 namespace {
@@ -1969,6 +2035,7 @@ int poisfft_batch_autotune(poisfft_batch* b, void* const phi[], const void* cons
     return rc;
   }
   rc = batch_apply(b, cfg[best]);
+  for (int c = 0; c < POISFFT_BATCH_TUNE_CANDIDATES; c++) b->tuned[c] = cfg[c];
   if (ms)
     for (int c = 0; c < POISFFT_BATCH_TUNE_CANDIDATES; c++) ms[c] = t[c];
   if (chosen) *chosen = best;
@@ -1981,6 +2048,26 @@ int poisfft_batch_solve_sequential(poisfft_batch* b, void* const phi[], const vo
     const int rc = poisfft_solve(b->plans[i], phi[i], g[i], stream);
     if (rc != POISFFT_OK) return rc;
   }
+  return POISFFT_OK;
+}
+
+int poisfft_batch_select(poisfft_batch* b, int candidate) {
+  if (!b || candidate < 0 || candidate >= POISFFT_BATCH_TUNE_CANDIDATES || b->tuned[candidate].empty())
+    return POISFFT_ERR_INVALID_ARG;
+  return batch_apply(b, b->tuned[candidate]);
+}
+
+int poisfft_batch_info(const poisfft_batch* b, int64_t out[3]) {
+  if (!b || !out) return POISFFT_ERR_INVALID_ARG;
+  int64_t bytes = 0, launches = 0, points = 0;
+  for (const poisfft_plan* p : b->plans) {
+    for (const SweepLaunch& L : p->sweeps) bytes += L.bytes;
+    launches += (int64_t)p->sweeps.size();
+    points += (int64_t)p->nx * p->ny * p->nz;
+  }
+  out[0] = bytes;
+  out[1] = launches;
+  out[2] = points;
   return POISFFT_OK;
 }
 

@@ -117,3 +117,16 @@ def test_bf16x3_needs_a_1024_point_strided_axis(pb):
     assert rc in (pb.OK, pb.ERR_CUDA)
     if rc == pb.OK:
         pb.destroy(plan)
+
+
+def test_injected_size_fault_is_reported_before_any_cuda_call(pb, monkeypatch):
+    """Host-side fault injection: POISFFT_FAULT=size makes planning report
+    an unsupported size; without the variable the same plan is valid."""
+    monkeypatch.setenv("POISFFT_FAULT", "size")
+    rc, plan = pb.plan_create((32, 32, 32), (1, 1, 1), (0, 2, 4), 1, 0)
+    assert rc == pb.ERR_UNSUPPORTED_SIZE and not plan.value
+    monkeypatch.delenv("POISFFT_FAULT")
+    rc, plan = pb.plan_create((32, 32, 32), (1, 1, 1), (0, 2, 4), 1, 0)
+    assert rc in (pb.OK, pb.ERR_CUDA)
+    if rc == pb.OK:
+        pb.destroy(plan)
