@@ -667,6 +667,15 @@ def run_batch(args):
         plain_by_config[cname] = timed(batch.solve_sequential, args.steps) / args.steps
     batch.select(chosen)
     ms_plain_best = min(plain_by_config.values()) * args.steps
+    # one persistent launch per sweep phase over all problems
+    persistent = None
+    try:
+        for _ in range(max(1, args.warmup)):
+            batch.solve_persistent(phis, gs, stream)
+        ms_pers = timed(batch.solve_persistent, args.steps)
+        persistent = {"ms_per_step": ms_pers / args.steps, "value": throughput(npts, args.steps, 1, ms_pers / 1e3)}
+    except pb.PoisFFTError as e:
+        persistent = {"unavailable": str(e)}
     assert batch.check(stream) == pb.OK
     value = throughput(npts, args.steps, 1, ms_graph / 1e3)
     err = None
@@ -733,6 +742,7 @@ def run_batch(args):
                    "l2": "inputs larger than L2 (2.7 GB over the batch)"},
         "plain_ms_per_step": ms_plain / args.steps, "plain_ms_per_step_by_config": plain_by_config,
         "speedup_vs_best_plain": ms_plain_best / ms_graph, "speedup_vs_plain_same_tiles": ms_plain / ms_graph,
+        "persistent_phases": persistent,
         "create_s": t_create, "max_rel_err_vs_fp64": err, "checked_problems": None if err is None else len(probs),
         "autotune": {"kept": pb.Batch.TUNE_CANDIDATES[chosen],
                      "ms_per_replay": dict(zip(pb.Batch.TUNE_CANDIDATES, tune_ms)), "seconds": t_tune},

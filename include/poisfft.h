@@ -230,21 +230,26 @@ int poisfft_plan_autotune(poisfft_plan* plan, void* stream);
  *   default tile shapes (poisfft_batch_autotune tunes them in the batch's
  *   own setting).  Fails with the first failing plan's status.
  * poisfft_batch_solve: solves every problem (phi[i], g[i] as in
- *   poisfft_solve) on `stream`.  The problems' launches run on forked
+ *   poisfft_solve) on `stream` (persistently when the tuner chose that).  The problems' launches run on forked
  *   streams inside one CUDA graph, captured on the first call and replayed
  *   while the pointers and the stream are unchanged (re-captured otherwise).
  *   Capture happens on `stream`, so `stream` must not be the legacy default
  *   stream (use a created stream).
  * poisfft_batch_solve_sequential: the same problems one after another on
  *   `stream` without a graph (the plain form, for comparison).
- * poisfft_batch_autotune: tile tuning in the batch's own setting.  Times
- *   the whole graph (one capture, then 4 replays on `stream`) under each of
- *   POISFFT_BATCH_TUNE_CANDIDATES configurations of the general-kernel tile
- *   shapes: 0 = the shapes as created, 1 = every strided tile and x line
- *   block halved, 2 = every plan tuned alone (poisfft_plan_autotune); keeps
- *   the fastest.  phi and g as in poisfft_batch_solve (phi is overwritten
- *   with solutions).  ms (may be NULL) receives the milliseconds per graph
- *   replay of each candidate, chosen (may be NULL) the kept one.
+ * poisfft_batch_autotune: tuning in the batch's own setting.  Times the
+ *   whole batch (one capture or work-list build, then 4 solves on `stream`)
+ *   under each of POISFFT_BATCH_TUNE_CANDIDATES configurations: 0 = the
+ *   tile shapes as created, 1 = every strided tile and x line block halved,
+ *   2 = every plan's tiles tuned alone (poisfft_plan_autotune), 3 = the
+ *   shapes as created with each 3D general-path problem's sweep order (the
+ *   strided axis whose sweep carries the divide: z or y) chosen by timing
+ *   both alone, 4 = the shapes as created run as persistent phase launches
+ *   (poisfft_batch_solve_persistent; skipped, at 1e30 ms, for batches with
+ *   specialised plans); keeps the fastest, and poisfft_batch_solve then
+ *   runs it.  phi and g as in poisfft_batch_solve (phi is overwritten with
+ *   solutions).  ms (may be NULL) receives the milliseconds per batch solve
+ *   of each candidate, chosen (may be NULL) the kept one.
  *   Synchronises `stream`; the next poisfft_batch_solve re-captures the
  *   graph.  Returns POISFFT_OK, INVALID_ARG, ALLOC or CUDA (on failure the
  *   shapes as created are restored).
@@ -255,7 +260,19 @@ int poisfft_batch_create(poisfft_batch** out, int count, const int dims[], const
                          const int bc[], int approx, int dtype);
 int poisfft_batch_solve(poisfft_batch* batch, void* const phi[], const void* const g[], void* stream);
 int poisfft_batch_solve_sequential(poisfft_batch* batch, void* const phi[], const void* const g[], void* stream);
-#define POISFFT_BATCH_TUNE_CANDIDATES 3
+/* poisfft_batch_solve_persistent: the same solves as poisfft_batch_solve as
+ * one persistent launch per sweep phase: phase p runs launch p of every
+ * problem (x sweeps, strided sweeps, separate divides) from a device work
+ * list of (problem, tile) items, largest problems first; CTAs take tiles
+ * from an atomic counter and never wait on one another.  The work lists are
+ * built and uploaded on the first call and again whenever phi / g change
+ * (synchronously; later calls only enqueue a 4-byte memset and one launch
+ * per phase on `stream`).  Plans on the specialised FP32 kernels
+ * (power-of-two lengths 64..1024 with fitting BCs) are not in the lists:
+ * POISFFT_ERR_NOT_IMPLEMENTED.  Returns POISFFT_OK, INVALID_ARG,
+ * MISALIGNED, ALLOC or CUDA. */
+int poisfft_batch_solve_persistent(poisfft_batch* batch, void* const phi[], const void* const g[], void* stream);
+#define POISFFT_BATCH_TUNE_CANDIDATES 5
 int poisfft_batch_autotune(poisfft_batch* batch, void* const phi[], const void* const g[], void* stream,
                            double ms[POISFFT_BATCH_TUNE_CANDIDATES], int* chosen);
 int poisfft_batch_check(poisfft_batch* batch, void* stream);

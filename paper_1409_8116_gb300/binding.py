@@ -51,6 +51,7 @@ EXPORTED = [
     "poisfft_batch_create",
     "poisfft_batch_solve",
     "poisfft_batch_solve_sequential",
+    "poisfft_batch_solve_persistent",
     "poisfft_batch_autotune",
     "poisfft_batch_check",
     "poisfft_batch_info",
@@ -136,7 +137,7 @@ def _load():
     lib.poisfft_batch_info.restype = ctypes.c_int
     lib.poisfft_batch_select.argtypes = [ctypes.c_void_p, ctypes.c_int]
     lib.poisfft_batch_select.restype = ctypes.c_int
-    for nm in ("poisfft_batch_solve", "poisfft_batch_solve_sequential"):
+    for nm in ("poisfft_batch_solve", "poisfft_batch_solve_sequential", "poisfft_batch_solve_persistent"):
         getattr(lib, nm).argtypes = [ctypes.c_void_p, vpp, vpp, ctypes.c_void_p]
         getattr(lib, nm).restype = ctypes.c_int
     lib.poisfft_solve_refined.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
@@ -424,7 +425,14 @@ class Batch:
         if rc != OK:
             raise PoisFFTError(rc, "poisfft_batch_solve_sequential")
 
-    TUNE_CANDIDATES = ("as created", "tiles halved", "each plan tuned alone")
+    TUNE_CANDIDATES = ("as created", "tiles halved", "each plan tuned alone", "sweep order tuned per problem",
+                       "persistent phase launches")
+
+    def solve_persistent(self, phis, gs, stream=None):
+        """One persistent launch per sweep phase over all problems."""
+        rc = lib.poisfft_batch_solve_persistent(self._b, self._ptrs(phis), self._ptrs(gs), _stream(stream))
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_batch_solve_persistent")
 
     def autotune(self, phis, gs, stream=None):
         """Times the batch graph under each tile configuration and keeps the

@@ -14,6 +14,8 @@
 // line may carry two independent real lines in its real and imaginary parts.
 #pragma once
 
+#include <cuda.h>
+
 #include <stdint.h>
 
 namespace pf {
@@ -162,6 +164,19 @@ struct PairDivideArgs {
   const void* lam_z;
   double scale;
   int singular;
+};
+
+// One launch of one problem in a batch phase (batch_phase_kernel): the
+// launch's arguments, its tensor map (strided sweeps; TMA reads it from
+// global memory, hence the 64-byte alignment) and, for the separate divide,
+// its grid.
+struct __align__(64) BatchItem {
+  CUtensorMap map;
+  XArgs xa;
+  StridedArgs sa;
+  PairDivideArgs pda;
+  int kind;               // 0 x sweep, 1 strided sweep, 4 separate divide
+  int gx, gy;             // separate divide: its grid of 256-thread blocks
 };
 
 }  // namespace pf

@@ -28,6 +28,12 @@ cudaError_t launch_strided_sweep(const CUtensorMap& map, const StridedArgs& a, u
 template <typename T>
 cudaError_t launch_pair_divide(const PairDivideArgs& a, cudaStream_t s);
 
+// Persistent batch phase (sweep_kernels.cuh); occ != nullptr: no launch,
+// *occ = resident CTAs per SM for `smem`.
+template <typename T>
+cudaError_t launch_batch_phase(int kind, const BatchItem* items, const int* first, int nitems, int total,
+                               int* counter, int bar_off, unsigned grid, size_t smem, cudaStream_t s, int* occ);
+
 // Specialised FP32 two-pass kernels (fast_f32.cu) for line lengths M in
 // {64, 128, 256, 512, 1024}: radices R1 x R2 and the tile width W.
 bool fast_shape(int M, int* R1, int* R2, int* W);

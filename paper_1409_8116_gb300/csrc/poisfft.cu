@@ -457,6 +457,7 @@ struct poisfft_plan {
   void* stage_phi = nullptr;
   float* refine_r = nullptr;         // FP32 residual / correction of poisfft_solve_refined
   int refinements = 2;               // POISFFT_MIXED plans: refinement steps of poisfft_solve
+  int fused_axis = 0;                // general 3D plans: the strided axis whose sweep divides
   size_t field_bytes = 0;
   bool profiling = false;
   std::vector<cudaEvent_t> events;   // (launches + 1) per profiled solve
@@ -939,6 +940,32 @@ int validate_args(int dims, const int64_t n[], const double L[], const int bc[],
   return POISFFT_OK;
 }
 
+// Sweep sequence of the general kernels with the eigenvalue divide fused
+// into the sweep of `fused_axis` (3D: 1 or 2; the other strided axis is
+// transformed forward before it and backward after it; 2D: 1).
+int plan_general_sequence(poisfft_plan* p, int fused_axis, std::vector<SweepLaunch>& sw) {
+  SweepLaunch Ls;
+  int rc;
+  sw.clear();
+  const int other = fused_axis == 2 ? 1 : 2;
+  if ((rc = plan_x_sweep(p, 0, Ls)) != POISFFT_OK) return rc;
+  sw.push_back(Ls);
+  if (p->dims == 3) {
+    if ((rc = plan_strided_sweep(p, other, 0, Ls)) != POISFFT_OK) return rc;
+    sw.push_back(Ls);
+  }
+  if ((rc = plan_strided_sweep(p, fused_axis, 2, Ls)) != POISFFT_OK) return rc;
+  sw.push_back(Ls);
+  if (p->dims == 3) {
+    if ((rc = plan_strided_sweep(p, other, 1, Ls)) != POISFFT_OK) return rc;
+    sw.push_back(Ls);
+  }
+  if ((rc = plan_x_sweep(p, 1, Ls)) != POISFFT_OK) return rc;
+  sw.push_back(Ls);
+  p->fused_axis = fused_axis;
+  return POISFFT_OK;
+}
+
 // Everything of a plan that needs no device: axes with their FP64 tables,
 // the workspace shape, tiles and the sweep sequence.  general_only plans
 // use the general kernels only and no separate pair-divide pass, so their
@@ -1023,21 +1050,7 @@ int plan_host(poisfft_plan* p, const PlanArgs& a, bool general_only) {
     if ((rc = plan_x_sweep(p, 1, Ls)) != POISFFT_OK) return rc;
     sw.push_back(Ls);
   } else {
-    if ((rc = plan_x_sweep(p, 0, Ls)) != POISFFT_OK) return rc;
-    sw.push_back(Ls);
-    const int fused_axis = dims == 3 ? 2 : 1;
-    if (dims == 3) {
-      if ((rc = plan_strided_sweep(p, 1, 0, Ls)) != POISFFT_OK) return rc;
-      sw.push_back(Ls);
-    }
-    if ((rc = plan_strided_sweep(p, fused_axis, 2, Ls)) != POISFFT_OK) return rc;
-    sw.push_back(Ls);
-    if (dims == 3) {
-      if ((rc = plan_strided_sweep(p, 1, 1, Ls)) != POISFFT_OK) return rc;
-      sw.push_back(Ls);
-    }
-    if ((rc = plan_x_sweep(p, 1, Ls)) != POISFFT_OK) return rc;
-    sw.push_back(Ls);
+    if ((rc = plan_general_sequence(p, dims == 3 ? 2 : 1, sw)) != POISFFT_OK) return rc;
   }
   p->sweeps = sw;
   if (a.dtype == POISFFT_BF16X3) {
@@ -1839,6 +1852,20 @@ struct poisfft_batch {
   std::vector<void*> phi_cached;
   cudaStream_t stream_cached = nullptr;
   std::vector<std::vector<SweepLaunch>> tuned[POISFFT_BATCH_TUNE_CANDIDATES];  // the last tuner's candidates
+  // persistent phase launches (poisfft_batch_solve_persistent)
+  struct Phase {
+    int group = 0;                     // sweep phase; the groups of one phase run concurrently
+    int kind = 0;                      // launch kind of every item (0, 1 or 4)
+    int nitems = 0, total = 0, bar_off = 0;
+    size_t smem = 0, items_off = 0, first_off = 0;
+    unsigned grid = 0;
+  };
+  std::vector<Phase> phases;
+  bool persistent = false;             // poisfft_batch_solve runs the persistent phases (tuner's choice)
+  unsigned char* pdev = nullptr;       // work lists (BatchItem arrays and tile offsets) of every phase
+  int* pctr = nullptr;                 // one tile counter per phase
+  std::vector<const void*> p_g;        // the pointers the work lists were built for
+  std::vector<void*> p_phi;
 };
 
 namespace {
@@ -1849,6 +1876,8 @@ void free_batch(poisfft_batch* b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->pdev) cudaFree(b->pdev);
+  if (b->pctr) cudaFree(b->pctr);
   for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
   for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
@@ -1876,6 +1905,142 @@ void batch_drop_graph(poisfft_batch* b) {
   if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
   b->g_cached.clear();
   b->phi_cached.clear();
+  b->p_g.clear();  // the work lists hold the tile shapes too
+  b->p_phi.clear();
+}
+
+// Work lists of the persistent phases: phase p holds launch p of every
+// problem that has one, in descending order of tiles.  The tile shapes are
+// those of the plans (tuned or not); x sweeps get the problem's g / phi.
+template <typename T>
+int batch_build_phases(poisfft_batch* b, void* const phi[], const void* const g[]) {
+  size_t nph = 0;
+  for (poisfft_plan* p : b->plans) {
+    for (const SweepLaunch& L : p->sweeps)
+      if (L.kind == 2 || L.kind == 3) return POISFFT_ERR_NOT_IMPLEMENTED;  // specialised kernels: not in the lists
+    nph = std::max(nph, p->sweeps.size());
+  }
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return POISFFT_ERR_CUDA;
+  std::vector<unsigned char> host;
+  auto grow = [&](size_t bytes, size_t align) {
+    const size_t off = (host.size() + align - 1) / align * align;
+    host.resize(off + bytes);
+    return off;
+  };
+  // shared-memory classes: tiles up to 72 KB run three CTAs per SM, up to
+  // 110 KB two, larger ones one; each class is its own launch, so one large
+  // tile does not lower the occupancy of the whole phase
+  auto smem_class = [](size_t smem) { return smem <= 72 * 1024 ? 0 : (smem <= 110 * 1024 ? 1 : 2); };
+  b->phases.clear();
+  for (size_t ph = 0; ph < nph; ph++)
+  for (int kind : {0, 1, 4})
+  for (int cls = 0; cls < 3; cls++) {
+    std::vector<BatchItem> items;
+    std::vector<long long> tiles;
+    size_t smem = 16;
+    for (size_t i = 0; i < b->plans.size(); i++) {
+      poisfft_plan* p = b->plans[i];
+      if (ph >= p->sweeps.size()) continue;
+      const SweepLaunch& L = p->sweeps[ph];
+      if (L.kind != kind || smem_class(L.kind == 4 ? 0 : L.smem) != cls) continue;
+      BatchItem it;
+      memset(&it, 0, sizeof(it));
+      long long nt = L.grid;
+      if (L.kind == 0) {
+        it.kind = 0;
+        it.xa = L.xa;
+        it.xa.g = g[i];
+        it.xa.phi = phi[i];
+        it.xa.ny = p->ny;
+        it.xa.g_sy = it.xa.phi_sy = p->nx;
+        it.xa.g_sz = it.xa.phi_sz = (long long)p->nx * p->ny;
+        smem = std::max(smem, L.smem);
+      } else if (L.kind == 1) {
+        it.kind = 1;
+        it.sa = L.sa;
+        it.map = p->maps[L.map];
+        smem = std::max(smem, L.smem);
+      } else {
+        it.kind = 4;
+        it.pda = L.pda;
+        it.gx = (int)(((long long)L.pda.ncols * L.pda.ny + 255) / 256);
+        it.gy = L.pda.nz < 65535 ? L.pda.nz : 65535;
+        nt = (long long)it.gx * it.gy;
+      }
+      items.push_back(it);
+      tiles.push_back(nt);
+    }
+    std::vector<int> order(items.size());
+    for (size_t k = 0; k < order.size(); k++) order[k] = (int)k;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return tiles[x] > tiles[y]; });
+    if (items.empty()) continue;
+    b->phases.push_back(poisfft_batch::Phase());
+    poisfft_batch::Phase& P = b->phases.back();
+    P.group = (int)ph;
+    P.kind = kind;
+    P.nitems = (int)items.size();
+    P.items_off = grow(items.size() * sizeof(BatchItem), 64);
+    P.first_off = grow(items.size() * sizeof(int), 16);
+    long long total = 0;
+    for (size_t k = 0; k < order.size(); k++) {
+      memcpy(host.data() + P.items_off + k * sizeof(BatchItem), &items[order[k]], sizeof(BatchItem));
+      const int f = (int)total;
+      memcpy(host.data() + P.first_off + k * sizeof(int), &f, sizeof(int));
+      total += tiles[order[k]];
+    }
+    if (total > 0x7fffffffLL) return POISFFT_ERR_UNSUPPORTED_SIZE;
+    P.total = (int)total;
+    P.bar_off = (int)((smem + 15) / 16 * 16);
+    P.smem = (size_t)P.bar_off + 16;
+    int occ = 0;
+    if (launch_batch_phase<T>(kind, nullptr, nullptr, 0, 0, nullptr, 0, 0, P.smem, nullptr, &occ) != cudaSuccess ||
+        occ < 1)
+      return POISFFT_ERR_CUDA;
+    P.grid = (unsigned)std::min<long long>(total, (long long)occ * sms);
+  }
+  if (b->pdev) { cudaFree(b->pdev); b->pdev = nullptr; }
+  if (b->pctr) { cudaFree(b->pctr); b->pctr = nullptr; }
+  if (dev_malloc(&b->pctr, std::max<size_t>(b->phases.size(), 1) * sizeof(int)) != cudaSuccess)
+    return POISFFT_ERR_ALLOC;
+  if (dev_malloc(&b->pdev, std::max<size_t>(host.size(), 64)) != cudaSuccess) return POISFFT_ERR_ALLOC;
+  if (cudaMemcpy(b->pdev, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess) return POISFFT_ERR_CUDA;
+  b->p_g.assign(g, g + b->plans.size());
+  b->p_phi.assign(phi, phi + b->plans.size());
+  return POISFFT_OK;
+}
+
+// Phase by phase; the classes of one phase run concurrently on the batch's
+// forked streams and join on `st` before the next phase.
+template <typename T>
+int batch_run_phases(poisfft_batch* b, cudaStream_t st) {
+  size_t k = 0;
+  while (k < b->phases.size()) {
+    size_t e = k;
+    while (e < b->phases.size() && b->phases[e].group == b->phases[k].group) e++;
+    NvtxRange range("poisfft batch phase");
+    const bool fork = e - k > 1;
+    if (fork && cudaEventRecord(b->fork, st) != cudaSuccess) return POISFFT_ERR_CUDA;
+    for (size_t q = k; q < e; q++) {
+      const poisfft_batch::Phase& P = b->phases[q];
+      cudaStream_t s = fork ? b->streams[(q - k) % b->streams.size()] : st;
+      if (fork && cudaStreamWaitEvent(s, b->fork, 0) != cudaSuccess) return POISFFT_ERR_CUDA;
+      if (cudaMemsetAsync(b->pctr + q, 0, sizeof(int), s) != cudaSuccess) return POISFFT_ERR_CUDA;
+      const BatchItem* items = reinterpret_cast<const BatchItem*>(b->pdev + P.items_off);
+      const int* first = reinterpret_cast<const int*>(b->pdev + P.first_off);
+      if (launch_batch_phase<T>(P.kind, items, first, P.nitems, P.total, b->pctr + q, P.bar_off, P.grid, P.smem, s,
+                                nullptr) != cudaSuccess)
+        return POISFFT_ERR_CUDA;
+      if (fork) {
+        cudaEvent_t j = b->joins[(q - k) % b->joins.size()];
+        if (cudaEventRecord(j, s) != cudaSuccess || cudaStreamWaitEvent(st, j, 0) != cudaSuccess)
+          return POISFFT_ERR_CUDA;
+      }
+    }
+    k = e;
+  }
+  return POISFFT_OK;
 }
 
 int batch_apply(poisfft_batch* b, const std::vector<std::vector<SweepLaunch>>& cfg) {
@@ -1886,6 +2051,72 @@ int batch_apply(poisfft_batch* b, const std::vector<std::vector<SweepLaunch>>& c
   }
   batch_drop_graph(b);
   return POISFFT_OK;
+}
+
+// General 3D plans whose sweeps are x and strided sweeps only can carry the
+// divide in either strided sweep (plan_general_sequence).
+bool order_tunable(const poisfft_plan* p) {
+  if (p->dims != 3 || p->fast) return false;
+  for (const SweepLaunch& L : p->sweeps)
+    if (L.kind != 0 && L.kind != 1) return false;
+  return true;
+}
+
+// Re-plan the sweep sequence of a plan with the divide in `fused_axis`
+// (tile shapes as planned); the device tables are unchanged.
+int replan_fused_axis(poisfft_plan* p, int fused_axis) {
+  std::vector<SweepLaunch> sw;
+  int rc = plan_general_sequence(p, fused_axis, sw);
+  if (rc != POISFFT_OK) return rc;
+  p->sweeps = sw;
+  patch_general(p);
+  return encode_maps(p);
+}
+
+// Time each order-tunable plan alone with the divide in z and in y (one
+// warm-up and three timed solves each) and keep the faster order.
+int batch_tune_sweep_order(poisfft_batch* b, cudaStream_t st) {
+  size_t fb = 0;
+  for (const poisfft_plan* p : b->plans)
+    if (order_tunable(p)) fb = std::max(fb, p->field_bytes);
+  if (fb == 0) return POISFFT_OK;
+  void* g = nullptr;
+  void* phi = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = POISFFT_OK;
+  if (dev_malloc(&g, fb) != cudaSuccess || dev_malloc(&phi, fb) != cudaSuccess ||
+      cudaMemsetAsync(g, 0, fb, st) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess)
+    rc = POISFFT_ERR_ALLOC;
+  for (poisfft_plan* p : b->plans) {
+    if (rc != POISFFT_OK) break;
+    if (!order_tunable(p)) continue;
+    float best_ms = 1e30f;
+    int best_axis = 2;
+    for (int axis : {2, 1}) {
+      if ((rc = replan_fused_axis(p, axis)) != POISFFT_OK) break;
+      if ((rc = solve_core(p, phi, g, st)) != POISFFT_OK) break;
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 3 && rc == POISFFT_OK; r++) rc = solve_core(p, phi, g, st);
+      cudaEventRecord(e1, st);
+      float ms = 0.f;
+      if (rc == POISFFT_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        rc = POISFFT_ERR_CUDA;
+      if (rc == POISFFT_OK && ms < best_ms * 0.97f) {  // the other order must win clearly
+        best_ms = ms;
+        best_axis = axis;
+      }
+    }
+    if (rc == POISFFT_OK) rc = replan_fused_axis(p, best_axis);
+    if (rc == POISFFT_OK && cudaMemsetAsync(p->ws, 0, p->ws_bytes, st) != cudaSuccess) rc = POISFFT_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess && rc == POISFFT_OK) rc = POISFFT_ERR_CUDA;
+  if (g) cudaFree(g);
+  if (phi) cudaFree(phi);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaGetLastError();
+  return rc;
 }
 
 std::vector<std::vector<SweepLaunch>> batch_snapshot(const poisfft_batch* b) {
@@ -1948,6 +2179,7 @@ int poisfft_batch_create(poisfft_batch** out, int count, const int dims[], const
 
 int poisfft_batch_solve(poisfft_batch* b, void* const phi[], const void* const g[], void* stream) {
   if (!b || !phi || !g) return POISFFT_ERR_INVALID_ARG;
+  if (b->persistent) return poisfft_batch_solve_persistent(b, phi, g, stream);
   const size_t cnt = b->plans.size();
   for (size_t i = 0; i < cnt; i++) {
     if (!phi[i] || !g[i]) return POISFFT_ERR_INVALID_ARG;
@@ -2004,6 +2236,18 @@ int poisfft_batch_autotune(poisfft_batch* b, void* const phi[], const void* cons
   for (size_t i = 0; rc == POISFFT_OK && i < b->plans.size(); i++) rc = poisfft_plan_autotune(b->plans[i], stream);
   if (rc != POISFFT_OK) return rc;
   cfg[2] = batch_snapshot(b);
+  // candidate 3: the shapes as created, with each 3D general-path problem's
+  // sweep order (which strided axis carries the divide) chosen by timing
+  // both orders alone
+  if ((rc = batch_apply(b, cfg[0])) != POISFFT_OK) return rc;
+  if ((rc = batch_tune_sweep_order(b, st)) != POISFFT_OK) {
+    batch_apply(b, cfg[0]);
+    return rc;
+  }
+  cfg[3] = batch_snapshot(b);
+  // candidate 4: the shapes as created, one persistent launch per phase
+  cfg[4] = cfg[0];
+  b->persistent = false;
 
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -2016,10 +2260,18 @@ int poisfft_batch_autotune(poisfft_batch* b, void* const phi[], const void* cons
   int best = 0;
   for (int c = 0; c < POISFFT_BATCH_TUNE_CANDIDATES && rc == POISFFT_OK; c++) {
     rc = batch_apply(b, cfg[c]);
-    if (rc == POISFFT_OK) rc = poisfft_batch_solve(b, phi, g, stream);  // capture and warm up
+    auto run = [&]() {
+      return c == 4 ? poisfft_batch_solve_persistent(b, phi, g, stream) : poisfft_batch_solve(b, phi, g, stream);
+    };
+    if (rc == POISFFT_OK) rc = run();  // capture (or build the work lists) and warm up
+    if (rc == POISFFT_ERR_NOT_IMPLEMENTED && c == 4) {  // specialised plans: no persistent form
+      rc = POISFFT_OK;
+      t[c] = 1e30;
+      continue;
+    }
     if (rc != POISFFT_OK) break;
     cudaEventRecord(e0, st);
-    for (int r = 0; r < kReps && rc == POISFFT_OK; r++) rc = poisfft_batch_solve(b, phi, g, stream);
+    for (int r = 0; r < kReps && rc == POISFFT_OK; r++) rc = run();
     cudaEventRecord(e1, st);
     float f = 0.f;
     if (rc == POISFFT_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&f, e0, e1) != cudaSuccess))
@@ -2035,11 +2287,37 @@ int poisfft_batch_autotune(poisfft_batch* b, void* const phi[], const void* cons
     return rc;
   }
   rc = batch_apply(b, cfg[best]);
+  b->persistent = best == 4;
   for (int c = 0; c < POISFFT_BATCH_TUNE_CANDIDATES; c++) b->tuned[c] = cfg[c];
   if (ms)
     for (int c = 0; c < POISFFT_BATCH_TUNE_CANDIDATES; c++) ms[c] = t[c];
   if (chosen) *chosen = best;
   return rc;
+}
+
+int poisfft_batch_solve_persistent(poisfft_batch* b, void* const phi[], const void* const g[], void* stream) {
+  if (!b || !phi || !g) return POISFFT_ERR_INVALID_ARG;
+  const size_t cnt = b->plans.size();
+  for (size_t i = 0; i < cnt; i++) {
+    if (!phi[i] || !g[i]) return POISFFT_ERR_INVALID_ARG;
+    const size_t es = b->plans[i]->esize;
+    if (((uintptr_t)phi[i] % es) != 0 || ((uintptr_t)g[i] % es) != 0) return POISFFT_ERR_MISALIGNED;
+  }
+  const bool f64 = b->plans[0]->esize == 8;
+  bool same = b->p_g.size() == cnt;
+  for (size_t i = 0; same && i < cnt; i++) same = b->p_g[i] == g[i] && b->p_phi[i] == phi[i];
+  if (!same) {
+    FaultScope fault;
+    const int rc = f64 ? batch_build_phases<double>(b, phi, g) : batch_build_phases<float>(b, phi, g);
+    if (rc != POISFFT_OK) {
+      cudaGetLastError();
+      b->p_g.clear();
+      b->p_phi.clear();
+      return rc;
+    }
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  return f64 ? batch_run_phases<double>(b, st) : batch_run_phases<float>(b, st);
 }
 
 int poisfft_batch_solve_sequential(poisfft_batch* b, void* const phi[], const void* const g[], void* stream) {
@@ -2054,7 +2332,9 @@ int poisfft_batch_solve_sequential(poisfft_batch* b, void* const phi[], const vo
 int poisfft_batch_select(poisfft_batch* b, int candidate) {
   if (!b || candidate < 0 || candidate >= POISFFT_BATCH_TUNE_CANDIDATES || b->tuned[candidate].empty())
     return POISFFT_ERR_INVALID_ARG;
-  return batch_apply(b, b->tuned[candidate]);
+  const int rc = batch_apply(b, b->tuned[candidate]);
+  b->persistent = rc == POISFFT_OK && candidate == 4;
+  return rc;
 }
 
 int poisfft_batch_info(const poisfft_batch* b, int64_t out[3]) {

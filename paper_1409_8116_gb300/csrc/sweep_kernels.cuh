@@ -32,8 +32,11 @@ template <> struct Emax<double> { static constexpr int value = 16; };
 // Three CTAs per SM (80 registers, a few hundred bytes of spills): the sweep
 // waits on its loads, and the third CTA hides more of that latency than the
 // spills cost (512^3, x forward 0.85 -> 0.69 ms before the cp.async staging).
+// One CTA's work (line pairs bid * lines ...) of the contiguous sweep; the
+// kernel below runs it for blockIdx.x, the batch phase kernel for the tiles
+// it takes from its work list.
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 3) x_sweep_kernel(const XArgs a) {
+__device__ __forceinline__ void x_sweep_body(const XArgs& a, const int bid) {
   constexpr int EMAX = Emax<T>::value;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
@@ -46,7 +49,7 @@ __global__ void __launch_bounds__(kThreads, 3) x_sweep_kernel(const XArgs a) {
   const int* perm = a.perm;
   const int nx = a.nx;
   const int M = a.ax.fft.M;
-  const long long row0 = (long long)blockIdx.x * 2 * a.lines;
+  const long long row0 = (long long)bid * 2 * a.lines;
   const int kind = a.mode == 0 ? a.ax.kfwd : a.ax.kinv;
   // field row r = y + ny*z of the CTA's first line; later rows by one 32-bit
   // fast division of (y0 + offset) by ny
@@ -151,6 +154,11 @@ __global__ void __launch_bounds__(kThreads, 3) x_sweep_kernel(const XArgs a) {
       }
     });
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 3) x_sweep_kernel(const XArgs a) {
+  x_sweep_body<T>(a, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -267,44 +275,42 @@ __device__ __forceinline__ void fused_divide_pairs(cx<T>* buf, const LAY lay, in
 // Three CTAs per SM (80 registers; the staging arrays of the pre-processing
 // spill to L1): 512 uneven batch problems 63.9 -> 60.8 ms against two CTAs
 // per SM with a 128-register cap (which in turn beat one CTA without a cap).
+// One tile (bid) of the strided sweep.  `bar` is an initialised mbarrier
+// whose phase `parity` completes when the tile's TMA boxes have landed; the
+// kernel below runs one tile per CTA, the batch phase kernel many.  Returns
+// false (uniformly) when the bounded wait for the boxes gave up.
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 3) strided_sweep_kernel(const __grid_constant__ CUtensorMap tmap,
-                                                                 const StridedArgs a) {
+__device__ __forceinline__ bool strided_sweep_body(const CUtensorMap* tmap, const StridedArgs& a, const int bid,
+                                                   uint64_t* bar, const uint32_t parity) {
   constexpr int EMAX = Emax<T>::value;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + a.bar_off);
   const ColTile lay{a.w, a.lw};
   cx<T>* scratch = buf + (size_t)a.rows_alloc * a.w;  // direct-DFT scratch or the Bluestein buffer
   const cx<T>* tables = reinterpret_cast<const cx<T>*>(a.tables);
   const cx<T>* mk = a.ax.mk_off >= 0 ? tables + a.ax.mk_off : nullptr;
   const int* perm = a.perm;
   const int n = a.ax.n;
-  const int tcol = blockIdx.x % a.ntile_c;
-  const int outer = blockIdx.x / a.ntile_c;
+  const int tcol = bid % a.ntile_c;
+  const int outer = bid / a.ntile_c;
   const int c0 = tcol * a.w;
 
   // ---- stage A: TMA boxes of the tile
-  if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
   if (threadIdx.x == 0) {
     const uint32_t box_bytes = (uint32_t)(2 * a.w * a.box_h * sizeof(T));
     mbar_arrive_expect_tx(bar, box_bytes * a.nbox);
     for (int b = 0; b < a.nbox; b++) {
       cx<T>* dst = buf + (size_t)b * a.box_h * a.w;
       if (a.axis_dim == 1)
-        tma_load_3d(dst, &tmap, bar, 2 * c0, b * a.box_h, outer);
+        tma_load_3d(dst, tmap, bar, 2 * c0, b * a.box_h, outer);
       else
-        tma_load_3d(dst, &tmap, bar, 2 * c0, outer, b * a.box_h);
+        tma_load_3d(dst, tmap, bar, 2 * c0, outer, b * a.box_h);
     }
   }
-  const bool ok = mbar_wait_bounded(bar, 0);
+  const bool ok = mbar_wait_bounded(bar, parity);
   if (__syncthreads_or(!ok)) {
     if (threadIdx.x == 0) atomicExch(a.err, 1);
-    return;
+    return false;
   }
 
   cx<T>* out = reinterpret_cast<cx<T>*>(a.data) + (size_t)outer * a.s_outer + c0;
@@ -329,7 +335,7 @@ __global__ void __launch_bounds__(kThreads, 3) strided_sweep_kernel(const __grid
           out[(size_t)k * a.s_axis + c] = post_value<T>(res, lay, decltype(kc)::value, n, k, c, mk, perm);
       });
     }
-    return;
+    return true;
   }
 
   if (a.ax.blu) {
@@ -362,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, 3) strided_sweep_kernel(const __grid
       const int k = e >> a.lw;
       if (c < ncol_valid) out[(size_t)k * a.s_axis + c] = post_value<T>(scratch, lay, a.ax.kinv, n, k, c, mk, perm);
     }
-    return;
+    return true;
   }
 
   if (a.dit_fused) {
@@ -383,7 +389,7 @@ __global__ void __launch_bounds__(kThreads, 3) strided_sweep_kernel(const __grid
           out[(size_t)k * a.s_axis + c] = post_value<T, true>(buf, lay, decltype(kc)::value, n, k, c, mk, perm);
       });
     }
-    return;
+    return true;
   }
 
   // ---- fused (plans with a direct-DFT pass): forward, divide by the eigenvalues, backward
@@ -430,20 +436,35 @@ __global__ void __launch_bounds__(kThreads, 3) strided_sweep_kernel(const __grid
     const int k = e >> a.lw;
     if (c < ncol_valid) out[(size_t)k * a.s_axis + c] = post_value<T>(buf, lay, a.ax.kinv, n, k, c, mk, perm);
   }
+  return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 3) strided_sweep_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                 const StridedArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + a.bar_off);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  strided_sweep_body<T>(&tmap, a, blockIdx.x, bar, 0);
 }
 
 // ---------------------------------------------------------------------------
 // eigenvalue divide for packed real x columns with periodic y or z
 // ---------------------------------------------------------------------------
+// Block (bx, by) of a gx x gy grid of 256-thread blocks: bx covers one (c, y)
+// plane, by strides over z with step gy.
 template <typename T>
-__global__ void __launch_bounds__(256) pair_divide_kernel(const PairDivideArgs a) {
-  // grid.x covers one (c, y) plane, grid.y strides over z
-  const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void pair_divide_body(const PairDivideArgs& a, int bx, int by, int gy) {
+  const uint32_t e = bx * 256u + threadIdx.x;
   if (e >= (uint32_t)a.ncols * (uint32_t)a.ny) return;
   const int y = (int)fdiv(e, a.dncols);
   const int c = (int)(e - (uint32_t)y * (uint32_t)a.ncols);
   const int yn = a.per_y ? (y == 0 ? 0 : a.ny - y) : y;
-  for (int z = blockIdx.y; z < a.nz; z += gridDim.y) {
+  for (int z = by; z < a.nz; z += gy) {
     const int zn = a.per_z ? (z == 0 ? 0 : a.nz - z) : z;
     if (z > zn || (z == zn && y > yn)) continue;  // the mirror element's thread does the pair
     cx<T>* ws = reinterpret_cast<cx<T>*>(a.data);
@@ -466,6 +487,71 @@ __global__ void __launch_bounds__(256) pair_divide_kernel(const PairDivideArgs a
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) pair_divide_kernel(const PairDivideArgs a) {
+  pair_divide_body<T>(a, blockIdx.x, blockIdx.y, gridDim.y);
+}
+
+// ---------------------------------------------------------------------------
+// batch phase kernel: one persistent launch runs launch p of every problem
+// ---------------------------------------------------------------------------
+// The work list holds one item per (problem, launch p) in descending order
+// of tiles; first[i] is the index of item i's first tile in the list.  CTAs
+// take tiles in order from a counter (zero before the launch), find their
+// item by binary search and run its body; no CTA waits on another.  The
+// mbarrier sits behind the largest tile (bar_off), and each strided tile
+// completes one of its phases.  A CTA whose bounded wait gave up stops (the
+// item's plan flag records it).
+// KIND: the launch kind of every item in the list (0 x sweep, 1 strided
+// sweep, 4 separate divide), so that each kernel holds one body only.
+template <typename T, int KIND>
+__global__ void __launch_bounds__(kThreads, 3)
+    batch_phase_kernel(const BatchItem* __restrict__ items, const int* __restrict__ first, int nitems, int total,
+                       int* counter, int bar_off) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + bar_off);
+  __shared__ int s_t;
+  // the item's arguments, copied so that the bodies read them from shared
+  // memory (a global-memory reference could alias the bodies' own stores)
+  __shared__ BatchItem s_item;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  uint32_t parity = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_t = atomicAdd(counter, 1);
+    __syncthreads();
+    const int t = s_t;
+    if (t >= total) break;
+    int lo = 0, hi = nitems - 1;  // the last item whose first tile is <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(&first[mid]) <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const int bid = t - __ldg(&first[lo]);
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(items + lo);
+      uint4* dst = reinterpret_cast<uint4*>(&s_item);
+      for (int e = threadIdx.x; e < (int)(sizeof(BatchItem) / 16); e += kThreads) dst[e] = __ldg(src + e);
+    }
+    __syncthreads();
+    if (KIND == 0) {
+      x_sweep_body<T>(s_item.xa, bid);
+    } else if (KIND == 1) {
+      // TMA reads the tensor map from global memory (not from shared memory)
+      const bool ok = strided_sweep_body<T>(&items[lo].map, s_item.sa, bid, bar, parity);
+      parity ^= 1;
+      if (!ok) break;
+    } else {
+      pair_divide_body<T>(s_item.pda, bid % s_item.gx, bid / s_item.gx, s_item.gy);
+    }
+    fence_proxy_async();
+    __syncthreads();  // the tile's shared memory is read before the next tile reuses it
+  }
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -485,6 +571,19 @@ cudaError_t launch_strided_sweep(const CUtensorMap& map, const StridedArgs& a, u
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<grid, kThreads, smem, s>>>(map, a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_batch_phase(int kind, const BatchItem* items, const int* first, int nitems, int total,
+                               int* counter, int bar_off, unsigned grid, size_t smem, cudaStream_t s, int* occ) {
+  auto k = kind == 0 ? batch_phase_kernel<T, 0> : (kind == 1 ? batch_phase_kernel<T, 1> : batch_phase_kernel<T, 4>);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, kThreads, smem);
+  k<<<grid, kThreads, smem, s>>>(items, first, nitems, total, counter, bar_off);
   return cudaGetLastError();
 }
 

@@ -114,3 +114,57 @@ def test_batch_autotune_keeps_results(pb):
         assert batch.check(stream) == pb.OK
         for phi, ref, p in zip(phis, refs, probs):
             assert O.rel_max_error(phi.cpu().numpy(), ref) < 1e-5, p
+        # every candidate (tile shapes, per-problem sweep order, persistent
+        # phase launches) solves every problem
+        for cand in range(len(pb.Batch.TUNE_CANDIDATES)):
+            batch.select(cand)
+            for x in phis:
+                x.fill_(float("nan"))
+            batch.solve(phis, gd, stream)
+            stream.synchronize()
+            assert batch.check(stream) == pb.OK
+            for phi, ref, p in zip(phis, refs, probs):
+                assert O.rel_max_error(phi.cpu().numpy(), ref) < 1e-5, (cand, p)
+
+
+@pytest.mark.parametrize("dtype,tol", [("f32", 1e-5), ("f64", 1e-12)])
+def test_persistent_phase_launches_match_oracle(pb, dtype, tol):
+    """One persistent launch per sweep phase over a (problem, tile) work
+    list gives every problem the oracle's solution; new contents behind the
+    same pointers reuse the lists, new pointers rebuild them."""
+    probs = _batch(40, 13)
+    npdt = np.float32 if dtype == "f32" else np.float64
+    gs, refs = _inputs(probs, npdt)
+    stream = torch.cuda.Stream()
+    with pb.Batch([(p["n"], p["Ls"], p["bcs"]) for p in probs], pb.FD2,
+                  pb.F32 if dtype == "f32" else pb.F64) as batch:
+        gd = [torch.from_numpy(g).cuda() for g in gs]
+        phis = [torch.full_like(x, float("nan")) for x in gd]
+        torch.cuda.synchronize()
+        batch.solve_persistent(phis, gd, stream)
+        stream.synchronize()
+        assert batch.check(stream) == pb.OK
+        for phi, ref, p in zip(phis, refs, probs):
+            assert O.rel_max_error(phi.cpu().numpy(), ref) < tol, p
+        for x in gd:
+            x.mul_(3.0)
+        batch.solve_persistent(phis, gd, stream)
+        stream.synchronize()
+        for phi, ref in zip(phis, refs):
+            assert O.rel_max_error(phi.cpu().numpy(), 3.0 * ref) < tol
+        phis2 = [torch.zeros_like(x) for x in gd]
+        batch.solve_persistent(phis2, gd, stream)
+        stream.synchronize()
+        phis3 = [torch.zeros_like(x) for x in gd]
+        batch.solve(phis3, gd, stream)  # the graph form: identical kernels per tile
+        stream.synchronize()
+        for a, b in zip(phis2, phis3):
+            assert torch.equal(a, b)
+
+
+def test_persistent_refuses_specialised_plans(pb):
+    with pb.Batch([((64, 64, 64), (1.0, 1.0, 1.0), (W.P, W.P, W.NS))], pb.FD2, pb.F32) as batch:
+        g = torch.zeros((64, 64, 64), device="cuda")
+        with pytest.raises(pb.PoisFFTError) as e:
+            batch.solve_persistent([torch.empty_like(g)], [g], torch.cuda.Stream())
+        assert e.value.status == pb.ERR_NOT_IMPLEMENTED
