@@ -9,7 +9,11 @@ namespace {
 template <int R1, int R2, int W, int MODE, int KIND>
 cudaError_t run_strided(const CUtensorMap& map, const fast::FastStridedArgs& a, unsigned grid, size_t smem,
                         cudaStream_t s) {
-  auto k = fast::fast_strided_kernel<R1, R2, W, MODE, KIND>;
+  void (*k)(const CUtensorMap, const fast::FastStridedArgs);
+  if constexpr (MODE == fast::FM_FUSED)
+    k = fast::fast_fused_kernel<R1, R2, W, KIND>;
+  else
+    k = fast::fast_strided_kernel<R1, R2, W, MODE, KIND>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);

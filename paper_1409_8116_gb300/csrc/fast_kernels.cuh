@@ -93,21 +93,18 @@ struct Shape {
 // Tile: W columns x M rows.  Thread t: column c = t % W, butterfly index
 // t / W.  Smem: TMA layout row*W + c, then padded layout
 // block*(R2*W + pad) + row*W + c.
-// Resident CTAs per SM (register budget): 768 threads for the single-
-// transform sweeps, 512 for the fused sweep (its registers would spill).
-template <int MODE, int NT> struct StridedMinBlocks {
-  static constexpr int value = (MODE == 2 ? 512 : 768) / NT;
-};
+// Forward (FM_FWD) or backward (FM_INV) transform of the swept axis, three
+// CTAs per SM (768 threads); the fused sweep is fast_fused_kernel.
 // Padding after every block of R2 rows in the padded layout (complex):
 // shifts consecutive blocks across the smem banks for narrow tiles.
 template <int W> struct BlockPad { static constexpr int value = W < 8 ? W : 8; };
 
 template <int R1, int R2, int W, int MODE, int KIND>
-__global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, StridedMinBlocks<MODE, W * Shape<R1, R2>::RMAX>::value)
+__global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, 768 / (W * Shape<R1, R2>::RMAX))
     fast_strided_kernel(const __grid_constant__ CUtensorMap tmap, const FastStridedArgs a) {
   constexpr int M = R1 * R2;
+  static_assert(MODE == FM_FWD || MODE == FM_INV, "fused sweeps run fast_fused_kernel");
   constexpr bool DCT = KIND != FK_DFT;
-  constexpr bool PAIR = KIND == FK_DCT_PAIR;
   constexpr int BS = R2 * W + BlockPad<W>::value;  // padded block stride (complex)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
@@ -146,7 +143,7 @@ __global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, StridedMinBlocks<MODE
   float2* out = a.data + (size_t)outer * a.s_outer + c0;
   const bool col_ok = c0 + c < a.ncols;
 
-  if (MODE == FM_FWD || MODE == FM_FUSED) {
+  if (MODE == FM_FWD) {
     // ---- DIF pass 1 from the TMA layout
     float2 u[R1];
     const bool act1 = bi < R2;
@@ -186,88 +183,21 @@ __global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, StridedMinBlocks<MODE
       __syncthreads();
     }
 
-    if (MODE == FM_FWD) {
-      if (act2 && col_ok) {
-#pragma unroll
-        for (int s2 = 0; s2 < R2; s2++) {
-          const int k = b + R1 * s2;
-          float2 x = y[s2];
-          if (DCT) {
-            const int kp = k == 0 ? 0 : M - k;
-            const float2 yp = sm[(kp % R1) * BS + (kp / R1) * W + c];
-            const float2 w = __ldg(&a.mk[k]);
-            x = cadd<float>(cmul<float>(w, x), cmulc<float>(yp, w));  // X_k = w Y_k + conj(w) Y_{M-k}
-          }
-          out[(size_t)k * a.s_axis + c] = x;
-        }
-      }
-      return;
-    }
-
-    // ---- fused: divide by the eigenvalues, then DIT pass A in registers
-    if (act2) {
-      const int col = c0 + c;
-      const float lam_o = __ldg(&a.lam_out[outer]);
-      const float lam_xo = PAIR ? 0.f : (col < a.ncols ? __ldg(&a.lam_in[col]) : 0.f) + lam_o;
-      // PAIR: the real and imaginary parts are x columns 2 col and 2 col + 1
-      const float lam_xo0 = PAIR ? (col < a.ncols ? __ldg(&a.lam_in[2 * col]) : 0.f) + lam_o : 0.f;
-      const float lam_xo1 = PAIR ? (col < a.ncols ? __ldg(&a.lam_in[2 * col + 1]) : 0.f) + lam_o : 0.f;
-      const bool zero_row = a.singular && col == 0 && outer == 0;
+    if (act2 && col_ok) {
 #pragma unroll
       for (int s2 = 0; s2 < R2; s2++) {
         const int k = b + R1 * s2;
-        if (KIND == FK_DFT) {
-          float f = __fdividef(a.scale, lam_xo + __ldg(&a.lam_ax[k]));
-          if (zero_row && k == 0) f = 0.f;
-          y[s2] = make_float2(y[s2].x * f, y[s2].y * f);
-        } else if (PAIR) {
-          // The column packs two real sequences: Y = Yu + i Yv with Yu, Yv
-          // Hermitian (Yu_k = (Y_k + conj(Y_{M-k})) / 2, Yv_k = (Y_k -
-          // conj(Y_{M-k})) / 2i); each part takes the step below with its own
-          // x eigenvalue, using Y*_{M-k} = conj(Y*_k).
-          const int prow = b == 0 ? (R2 - s2) % R2 : R2 - 1 - s2;
-          const float2 yp = sm[((R1 - b) % R1) * BS + prow * W + c];
-          const float2 yk = y[s2];
-          const float2 Yu = make_float2(0.5f * (yk.x + yp.x), 0.5f * (yk.y - yp.y));
-          const float2 Yv = make_float2(0.5f * (yk.y + yp.y), 0.5f * (yp.x - yk.x));
-          const float4 t = __ldg(&a.pk[k]);
-          float f0k = __fdividef(a.scale, lam_xo0 + t.x);
-          float f0m = k == 0 ? f0k : __fdividef(a.scale, lam_xo0 + t.y);
-          if (zero_row && k == 0) f0k = f0m = 0.f;
-          const float f1k = __fdividef(a.scale, lam_xo1 + t.x);
-          const float f1m = k == 0 ? f1k : __fdividef(a.scale, lam_xo1 + t.y);
-          // e^{i pi k / M} conj(Y)
-          const float2 cu = make_float2(t.z * Yu.x + t.w * Yu.y, t.w * Yu.x - t.z * Yu.y);
-          const float2 cv = make_float2(t.z * Yv.x + t.w * Yv.y, t.w * Yv.x - t.z * Yv.y);
-          const float al0 = f0k + f0m, be0 = f0k - f0m, al1 = f1k + f1m, be1 = f1k - f1m;
-          const float2 Vu = make_float2(al0 * Yu.x + be0 * cu.x, al0 * Yu.y + be0 * cu.y);
-          const float2 Vv = make_float2(al1 * Yv.x + be1 * cv.x, al1 * Yv.y + be1 * cv.y);
-          y[s2] = make_float2(Vu.x - Vv.y, Vu.y + Vv.x);
-        } else {
-          // DCT-II post, divide and DCT-III pre in one step: with
-          // X_k = w Y_k + conj(w) Y_{M-k}, X_{M-k} = i (w Y_k - conj(w) Y_{M-k}),
-          // V_k = conj(w) (f_k X_k - i f_{M-k} X_{M-k})
-          //     = (f_k + f_{M-k}) Y_k + (f_k - f_{M-k}) conj(w)^2 Y_{M-k};  k = 0: 2 f_0 Y_0
-          // partner M-k: block (R1-b) mod R1, row R2-1-s2 (b > 0) or (R2-s2) mod R2 (b = 0)
-          const int prow = b == 0 ? (R2 - s2) % R2 : R2 - 1 - s2;
-          const float2 yp = sm[((R1 - b) % R1) * BS + prow * W + c];
-          const float4 t = __ldg(&a.pk[k]);
-          float fk = __fdividef(a.scale, lam_xo + t.x);
-          if (zero_row && k == 0) fk = 0.f;
-          const float fm = k == 0 ? fk : __fdividef(a.scale, lam_xo + t.y);
-          const float2 cyp = make_float2(t.z * yp.x - t.w * yp.y, t.z * yp.y + t.w * yp.x);
-          const float al = fk + fm, be = fk - fm;
-          y[s2] = make_float2(al * y[s2].x + be * cyp.x, al * y[s2].y + be * cyp.y);
+        float2 x = y[s2];
+        if (DCT) {
+          const int kp = k == 0 ? 0 : M - k;
+          const float2 yp = sm[(kp % R1) * BS + (kp / R1) * W + c];
+          const float2 w = __ldg(&a.mk[k]);
+          x = cadd<float>(cmul<float>(w, x), cmulc<float>(yp, w));  // X_k = w Y_k + conj(w) Y_{M-k}
         }
+        out[(size_t)k * a.s_axis + c] = x;
       }
-      Dft<float, R2, true>::run(y);
     }
-    if (DCT) __syncthreads();  // partners have read this block
-    if (act2) {
-#pragma unroll
-      for (int s = 0; s < R2; s++) sm[b * BS + s * W + c] = y[s];
-    }
-    __syncthreads();
+    return;
   } else {
     // ---- backward only: DIT pass A from the TMA layout (natural order input)
     float2 y[R2];
@@ -310,6 +240,220 @@ __global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, StridedMinBlocks<MODE
 #pragma unroll
       for (int s = 0; s < R1; s++) out[(size_t)(j + R2 * s) * a.s_axis + c] = u[s];
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// fused sweep, divide as a pass of its own
+// ---------------------------------------------------------------------------
+// Forward transform of the swept axis (DIF passes 1 and 2), the divide by
+// the eigenvalue sums with the zero-mode fix, and the backward transform
+// (DIT passes A and B) in one launch.  No step keeps more than one radix
+// block of values in registers: the
+// forward pass 2 writes its coefficients back in place, the divide runs as a
+// separate pass in which one thread takes the coefficient pair (k, M-k) of a
+// column (both outputs of the pair step from both inputs, so every
+// coefficient is read and written once and the eigenvalue factors of the
+// pair are computed once), and the backward pass A reads the result.  At 80
+// registers three CTAs fit on an SM instead of two.
+//
+// Pair step per kind, with Y the forward spectrum of the swept axis,
+// f_j = scale / (lambda_other + lambda_axis[j]) and t = (c, s) =
+// (cos, sin)(pi k / M):
+//   FK_DFT:      V_k = f_k Y_k, V_{M-k} = f_{M-k} Y_{M-k};
+//   FK_DCT:      with al = f_k + f_{M-k}, be = f_k - f_{M-k},
+//                V_k     = al Y_k     + be e^{+i pi k/M} Y_{M-k},
+//                V_{M-k} = al Y_{M-k} + be e^{-i pi k/M} Y_k;
+//   FK_DCT_PAIR: Y = Yu + i Yv with Yu, Yv Hermitian; each part takes the
+//                FK_DCT step with its own x eigenvalue, and since each part's
+//                result is Hermitian, V_{M-k} = conj(Vu_k) + i conj(Vv_k).
+// k = 0 and k = M/2 pair with themselves (be = 0; both writes agree).
+//
+// Shared memory: the tile (M x W complex) without padding; between the
+// passes block b, row q sits at row q ^ (b & 1) of the block, which spreads
+// the four blocks a warp touches at once over both halves of the banks.
+// The pair table pk[0 .. M/2] follows the tile, copied in by the bulk-copy
+// engine together with the tile.  Pass twiddles w^(j s), s = s0 + D s1
+// (D = 8 for R1 = 32, 4 for R1 = 16), are applied as the two factors
+// w^(j s0) and w^(j D s1), so a thread loads R1/D - 1 + D - 1 table values
+// instead of R1 - 1 (one more rounding where both factors apply).
+template <int R1> struct TwSplit { static constexpr int D = R1; };
+
+// u[s] *= w^(j s) (INV: conj), s = 1 .. R1 - 1, with tw[s * R2 + j] = w^(j s):
+// factor w^(j s0) on every s with s0 = s mod D > 0, then w^(j D s1) on every
+// s with s1 = s / D > 0 (one table value live at a time).
+template <int R1, int R2, bool INV>
+__device__ __forceinline__ void apply_pass_twiddles(float2* u, const float2* __restrict__ tw, int j) {
+  constexpr int D = TwSplit<R1>::D;
+  constexpr int NB = R1 / D;
+#pragma unroll
+  for (int s0 = 1; s0 < D; s0++) {
+    const float2 w = __ldg(&tw[s0 * R2 + j]);
+#pragma unroll
+    for (int s1 = 0; s1 < NB; s1++) u[s0 + D * s1] = INV ? cmulc<float>(u[s0 + D * s1], w) : cmul<float>(u[s0 + D * s1], w);
+  }
+#pragma unroll
+  for (int s1 = 1; s1 < NB; s1++) {
+    const float2 w = __ldg(&tw[D * s1 * R2 + j]);
+#pragma unroll
+    for (int s0 = 0; s0 < D; s0++) u[s0 + D * s1] = INV ? cmulc<float>(u[s0 + D * s1], w) : cmul<float>(u[s0 + D * s1], w);
+  }
+}
+
+template <int R1, int R2, int W, int KIND>
+__global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, 768 / (W * Shape<R1, R2>::RMAX))
+    fast_fused_kernel(const __grid_constant__ CUtensorMap tmap, const FastStridedArgs a) {
+  constexpr int M = R1 * R2;
+  constexpr int NT = W * Shape<R1, R2>::RMAX;
+  constexpr int KSTEP = NT / W;  // pair indices handled per column per sweep
+  constexpr int KIT = (M / 2) / KSTEP;
+  constexpr bool PAIR = KIND == FK_DCT_PAIR;
+  constexpr int BS = R2 * W;  // block stride (complex), no padding
+  constexpr uint32_t PK_BYTES = (M / 2 + 1) * 16;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  float2* sm = reinterpret_cast<float2*>(smem_raw);
+  float4* pks = reinterpret_cast<float4*>(smem_raw + (size_t)M * W * 8);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + (size_t)M * W * 8 + PK_BYTES);
+
+  const int tid = threadIdx.x;
+  const int c = tid % W;
+  const int bi = tid / W;
+  const int tcol = blockIdx.x % a.ntile_c;
+  const int outer = blockIdx.x / a.ntile_c;
+  const int c0 = tcol * W;
+  // position of (block b, row q, column c) between the passes
+  auto bpos = [&](int b, int q) { return b * BS + ((q ^ (b & 1)) * W) + c; };
+
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t box_bytes = (uint32_t)(2 * W * a.box_h * sizeof(float));
+    mbar_arrive_expect_tx(bar, box_bytes * a.nbox + PK_BYTES);
+    bulk_load_1d(pks, a.pk, PK_BYTES, bar);
+    for (int b = 0; b < a.nbox; b++) {
+      float2* dst = sm + (size_t)b * a.box_h * W;
+      if (a.axis_dim == 1)
+        tma_load_3d(dst, &tmap, bar, 2 * c0, b * a.box_h, outer);
+      else
+        tma_load_3d(dst, &tmap, bar, 2 * c0, outer, b * a.box_h);
+    }
+  }
+  const bool ok = mbar_wait_bounded(bar, 0);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) atomicExch(a.err, 1);
+    return;
+  }
+
+  // ---- DIF pass 1 (radix R1) from the TMA layout into the block layout
+  {
+    float2 u[R1];
+    const int j = bi;
+    if (bi < R2) {
+#pragma unroll
+      for (int q = 0; q < R1; q++) u[q] = sm[(j + R2 * q) * W + c];
+    }
+    __syncthreads();
+    if (bi < R2) {
+      Dft<float, R1, false>::run(u);
+      if (j != 0) apply_pass_twiddles<R1, R2, false>(u, a.tw, j);
+#pragma unroll
+      for (int s = 0; s < R1; s++) sm[bpos(s, j)] = u[s];
+    }
+    __syncthreads();
+  }
+  // ---- DIF pass 2 (radix R2) in place: coefficient k at block k % R1, row k / R1
+  if (bi < R1) {
+    float2 y[R2];
+#pragma unroll
+    for (int q = 0; q < R2; q++) y[q] = sm[bpos(bi, q)];
+    Dft<float, R2, false>::run(y);
+#pragma unroll
+    for (int s2 = 0; s2 < R2; s2++) sm[bpos(bi, s2)] = y[s2];
+  }
+  __syncthreads();
+
+  // ---- divide: coefficient pairs (k, M - k) of column c
+  {
+    const int col = c0 + c;
+    const bool cin = col < a.ncols;
+    const float lam_o = __ldg(&a.lam_out[outer]);
+    const float lam_xo = PAIR ? 0.f : (cin ? __ldg(&a.lam_in[col]) : 0.f) + lam_o;
+    const float lam_xo0 = PAIR ? (cin ? __ldg(&a.lam_in[2 * col]) : 0.f) + lam_o : 0.f;
+    const float lam_xo1 = PAIR ? (cin ? __ldg(&a.lam_in[2 * col + 1]) : 0.f) + lam_o : 0.f;
+    const bool zero_row = a.singular && col == 0 && outer == 0;
+    auto pair_step = [&](int k) {
+      const int km = (M - k) & (M - 1);
+      float2* pk_ = sm + bpos(k % R1, k / R1);
+      float2* pm_ = sm + bpos(km % R1, km / R1);
+      const float2 yk = *pk_, ym = *pm_;
+      const float4 t = pks[k];
+      float2 vk, vm;
+      if (KIND == FK_DFT) {
+        float fk = __fdividef(a.scale, lam_xo + t.x);
+        float fm = __fdividef(a.scale, lam_xo + t.y);
+        if (zero_row && k == 0) fk = fm = 0.f;
+        vk = make_float2(fk * yk.x, fk * yk.y);
+        vm = make_float2(fm * ym.x, fm * ym.y);
+      } else if (PAIR) {
+        const float2 Yu = make_float2(0.5f * (yk.x + ym.x), 0.5f * (yk.y - ym.y));
+        const float2 Yv = make_float2(0.5f * (yk.y + ym.y), 0.5f * (ym.x - yk.x));
+        float f0k = __fdividef(a.scale, lam_xo0 + t.x);
+        float f0m = k == 0 ? f0k : __fdividef(a.scale, lam_xo0 + t.y);
+        if (zero_row && k == 0) f0k = f0m = 0.f;
+        const float f1k = __fdividef(a.scale, lam_xo1 + t.x);
+        const float f1m = k == 0 ? f1k : __fdividef(a.scale, lam_xo1 + t.y);
+        const float2 cu = make_float2(t.z * Yu.x + t.w * Yu.y, t.w * Yu.x - t.z * Yu.y);
+        const float2 cv = make_float2(t.z * Yv.x + t.w * Yv.y, t.w * Yv.x - t.z * Yv.y);
+        const float al0 = f0k + f0m, be0 = f0k - f0m, al1 = f1k + f1m, be1 = f1k - f1m;
+        const float2 Vu = make_float2(al0 * Yu.x + be0 * cu.x, al0 * Yu.y + be0 * cu.y);
+        const float2 Vv = make_float2(al1 * Yv.x + be1 * cv.x, al1 * Yv.y + be1 * cv.y);
+        vk = make_float2(Vu.x - Vv.y, Vu.y + Vv.x);
+        vm = make_float2(Vu.x + Vv.y, Vv.x - Vu.y);
+      } else {
+        float fk = __fdividef(a.scale, lam_xo + t.x);
+        float fm = k == 0 ? fk : __fdividef(a.scale, lam_xo + t.y);
+        if (zero_row && k == 0) fk = fm = 0.f;
+        const float al = fk + fm, be = fk - fm;
+        // e^{+i pi k/M} Y_{M-k} and e^{-i pi k/M} Y_k
+        const float2 rm = make_float2(t.z * ym.x - t.w * ym.y, t.z * ym.y + t.w * ym.x);
+        const float2 rk = make_float2(t.z * yk.x + t.w * yk.y, t.z * yk.y - t.w * yk.x);
+        vk = make_float2(al * yk.x + be * rm.x, al * yk.y + be * rm.y);
+        vm = make_float2(al * ym.x + be * rk.x, al * ym.y + be * rk.y);
+      }
+      *pk_ = vk;
+      *pm_ = vm;
+    };
+#pragma unroll 4
+    for (int i = 0; i < KIT; i++) pair_step(bi + KSTEP * i);
+    if (bi == 0) pair_step(M / 2);
+  }
+  __syncthreads();
+
+  // ---- DIT pass A (radix R2) in place
+  if (bi < R1) {
+    float2 y[R2];
+#pragma unroll
+    for (int q = 0; q < R2; q++) y[q] = sm[bpos(bi, q)];
+    Dft<float, R2, true>::run(y);
+#pragma unroll
+    for (int s = 0; s < R2; s++) sm[bpos(bi, s)] = y[s];
+  }
+  __syncthreads();
+
+  // ---- DIT pass B (radix R1): natural-order output j + R2*s
+  float2* out = a.data + (size_t)outer * a.s_outer + c0;
+  if (bi < R2 && c0 + c < a.ncols) {
+    float2 u[R1];
+    const int j = bi;
+#pragma unroll
+    for (int q = 0; q < R1; q++) u[q] = sm[bpos(q, j)];
+    if (j != 0) apply_pass_twiddles<R1, R2, true>(u, a.tw, j);
+    Dft<float, R1, true>::run(u);
+#pragma unroll
+    for (int s = 0; s < R1; s++) out[(size_t)(j + R2 * s) * a.s_axis + c] = u[s];
   }
 }
 

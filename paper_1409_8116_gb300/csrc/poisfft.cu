@@ -415,6 +415,18 @@ EncodeTiledFn get_encode_fn() {
   return fn;
 }
 
+// Workspace row pitch (complex elements): the least p >= ncols whose row
+// stride, p * 2 * esize bytes, is 64 modulo 128.  Tile rows of the strided
+// sweeps then start on 64-byte boundaries and consecutive rows alternate
+// between the two halves of a 128-byte line; measured on the 1024^3 y sweeps
+// (1.67 -> 1.50 ms against the plain even pitch 514).
+long long workspace_pitch(long long ncols, size_t esize) {
+  const long long unit = 128 / (2 * (long long)esize);  // elements per 128 bytes
+  long long p = (ncols + unit - 1) / unit * unit + unit / 2;
+  if (p - unit >= ncols) p -= unit;
+  return p;
+}
+
 int pow2_floor(long long v) {
   int p = 1;
   while ((long long)p * 2 <= v) p *= 2;
@@ -765,6 +777,7 @@ void plan_fast_strided(poisfft_plan* p, int axis, int mode, SweepLaunch& L) {
   L.grid = (unsigned)((long long)s.ntile_c * nouter);
   const size_t tile_c = std::max<size_t>((size_t)R1 * (R2 * W + std::min(W, 8)), (size_t)M * W);
   L.smem = (tile_c * 8 + 15) / 16 * 16 + 16;
+  if (mode == fast::FM_FUSED) L.smem = (size_t)M * W * 8 + (size_t)(M / 2 + 1) * 16 + 16;  // tile, pair table, barrier
   L.bytes = 2LL * p->ncols * (long long)p->ny * p->nz * 8;
 }
 
@@ -1000,7 +1013,7 @@ int plan_host(poisfft_plan* p, const PlanArgs& a, bool general_only) {
   }
   p->singular = sing ? 1 : 0;
   p->ncols = p->r2c ? p->nx / 2 + 1 : (p->nx + 1) / 2;
-  p->pitch = (p->ncols + 1) / 2 * 2;
+  p->pitch = (int)workspace_pitch(p->ncols, p->esize);
   p->field_bytes = (size_t)p->nx * p->ny * p->nz * p->esize;
   p->ws_bytes = (size_t)p->pitch * 2 * p->esize * p->ny * p->nz;
 
@@ -1666,7 +1679,7 @@ extern "C" int poisfft_solve_noalloc(int dims, const int64_t n[], const double L
   if (!xper && any_per_yz) return POISFFT_ERR_NOT_IMPLEMENTED;
   // workspace size before any host planning: reject what cannot fit
   const long long ncols0 = xper ? args.n[0] / 2 + 1 : (args.n[0] + 1) / 2;
-  const long long pitch0 = (ncols0 + 1) / 2 * 2;
+  const long long pitch0 = workspace_pitch(ncols0, esize);
   const double ws_need = (double)pitch0 * 2 * esize * args.n[1] * args.n[2];
   if (ws_need + 256 > (double)kNoAllocBytes) return POISFFT_ERR_UNSUPPORTED_SIZE;
   // the table copies below read host vectors that live only during this call
