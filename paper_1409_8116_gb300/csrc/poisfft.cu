@@ -741,7 +741,7 @@ void plan_fast_x(poisfft_plan* p, int mode, SweepLaunch& L) {
   a.xsign = p->axes[0].bc == POISFFT_DS;
   const long long pairs = (a.nrows + 1) / 2;
   L.grid = (unsigned)((pairs + lpc - 1) / lpc);
-  L.smem = (size_t)lpc * R1 * (R2 + 1) * 8;
+  L.smem = (size_t)lpc * R1 * (R2 + 1) * 8 + 16;  // line buffer (also the staged rows), barrier
   const long long field = a.nrows * p->nx * 4LL;
   L.bytes = field + a.nrows * (long long)p->ncols * 8;
 }
@@ -787,6 +787,7 @@ void patch_fast(poisfft_plan* p) {
       L.fxa.tw = static_cast<const float2*>(p->ftw[0]);
       L.fxa.mk = static_cast<const float2*>(p->fmk[0]);
       L.fxa.ws = static_cast<float2*>(p->ws);
+      L.fxa.err = p->err;
     } else if (L.kind == 3) {
       const int a = L.axis;
       fast::FastStridedArgs& s = L.fsa;
