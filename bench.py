@@ -49,13 +49,14 @@ UNIT = "grid-pts/s"
 DEFAULT_WORKLOAD = "ppn_fd2_1024_f32"
 BC_NAME = {0: "P", 1: "DR", 2: "DS", 3: "NR", 4: "NS"}
 
-# DRAM traffic / algorithmic bytes of the specialised strided launches, from
-# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) on the
-# 512x512x1024 workload (profiles/traffic_fast_strided_512x512x1024.md).
+# DRAM traffic / algorithmic bytes of the five specialised sweeps, from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) on the
+# 512x512x1024 workload (profiles/traffic_fast_sweeps_512x512x1024.md).
 # Valid only while the kernel sources hash to TRAFFIC_SRC_SHA256.
-TRAFFIC_RATIO = {("strided_sweep", "fused"): 0.980, ("strided_sweep", "forward"): 0.979,
-                 ("strided_sweep", "backward"): 0.984}
-TRAFFIC_SRC_SHA256 = "cbf66f9cd05f35aa2f4eb5b148953195a64bc3f90dadbc41fbd60bc92cfde0ed"
+TRAFFIC_RATIO = {("x_sweep", "forward"): 0.993, ("strided_sweep", "forward"): 0.994,
+                 ("strided_sweep", "fused"): 1.011, ("strided_sweep", "backward"): 0.999,
+                 ("x_sweep", "backward"): 0.993}
+TRAFFIC_SRC_SHA256 = "a038c4129bcfca3bcf5d4a966619aeedaef415c8d79ee4e1da2786349ab3aa6f"
 TRAFFIC_SOURCES = ["fast_kernels.cuh", "fft_engine.cuh", "fast_f32.cu"]
 
 
@@ -352,12 +353,17 @@ def run_ours(args):
     dom_ms = per_launch_ms[dom] / nsolves
     peak, peak_kind = load_peaks()
     achieved = launches[dom]["bytes"] / (dom_ms / 1e3) / 1e9
-    key = (launches[dom]["kernel"], launches[dom]["mode"])
-    traffic = None
-    if key in TRAFFIC_RATIO and kernel_source_sha256() == TRAFFIC_SRC_SHA256:
-        traffic = TRAFFIC_RATIO[key] * launches[dom]["bytes"]
+    traffic_valid = kernel_source_sha256() == TRAFFIC_SRC_SHA256
+
+    def launch_traffic(i):
+        key = (launches[i]["kernel"], launches[i]["mode"])
+        return TRAFFIC_RATIO[key] * launches[i]["bytes"] if traffic_valid and key in TRAFFIC_RATIO else None
+
+    traffic = launch_traffic(dom)
     per_launch = [dict(launches[i], ms=per_launch_ms[i] / nsolves, share=shares[i],
-                       gbs=launches[i]["bytes"] / (per_launch_ms[i] / nsolves / 1e3) / 1e9)
+                       gbs=launches[i]["bytes"] / (per_launch_ms[i] / nsolves / 1e3) / 1e9,
+                       frac=launches[i]["bytes"] / (per_launch_ms[i] / nsolves / 1e3) / 1e9 / peak,
+                       traffic=launch_traffic(i))
                   for i in range(len(launches))]
     step_bytes = sum(l["bytes"] for l in launches)
 
