@@ -819,6 +819,40 @@ def run_pcg(args):
     ms, iters, rel, stats = timed(pb.PCG_MIXED, args.steps, args.warmup)
     clocks = sampler.stop()
     sol = phi.cpu().numpy()
+    # kernel launches of one mixed solve: residual + check, one Poisson solve
+    # (the preconditioner plan's sweeps) and two kernels per preconditioner
+    # application, six kernels per loop iteration (one loop iteration per
+    # application after the first), three closing kernels
+    with pb.Plan(n, spec["Ls"], (W.DS, W.DS, W.DS), pb.FD2, pb.F32) as pplan:
+        plan_launches = len(pplan.launches())
+    npre = stats["preconditioner_solves"]
+    launches_per_solve = 2 + npre * (plan_launches + 2) + (npre - 1) * 6 + 3
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end: g from pinned host memory, phi back to pinned host memory
+        gh = torch.from_numpy(g_host).pin_memory()
+        ph = torch.empty_like(gh).pin_memory()
+        e2e_steps = max(1, min(args.steps, 5))
+        e2e_it = 0
+        with torch.cuda.stream(stream):
+            for k in range(e2e_steps + 1):
+                if k == 1:
+                    stream.synchronize()
+                    t0 = time.perf_counter()
+                g.copy_(gh, non_blocking=True)
+                phi.zero_()
+                its, _ = solver.solve(phi, g, spec["tol"], 1000, stream, pb.PCG_MIXED)
+                ph.copy_(phi, non_blocking=True)
+                if k > 0:
+                    e2e_it += its
+            stream.synchronize()
+        t_e2e = time.perf_counter() - t0
+        e2e = {"value": npts * e2e_it / t_e2e, "unit": PCG_UNIT, "ms_per_solve": t_e2e / e2e_steps * 1e3,
+               "h2d_bytes_per_step": g.numel() * g.element_size(),
+               "d2h_bytes_per_step": phi.numel() * phi.element_size(),
+               "path": "g from pinned host memory, PCG solve (poisfft_pcg_solve), phi to pinned host memory"}
+        del gh, ph
     ms64, iters64, rel64, _ = timed(pb.PCG_F64, max(1, min(args.steps, 3)), 1)
     total_it = sum(iters)
     value = npts * total_it / (ms / 1e3)
@@ -858,7 +892,7 @@ def run_pcg(args):
                      "traffic": None, "kernel": "whole mixed PCG iteration (own kernels + FP32 Poisson solve)",
                      "bytes_per_cell_iteration": PCG_BYTES_OWN + PCG_BYTES_POISSON,
                      "peak_source": f"{peak_kind} hbm_gbs"},
-        "cpu_baseline": cpu, "e2e": None, "gpu_launches": None, "clocks": clocks,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_solve * args.steps, "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
     solver.close()
@@ -945,6 +979,38 @@ def run_learned(args):
     time.sleep(0.3)
     res = solve_set(ev["n"], ev["Ls"], a, g, net, args.steps, args.warmup)
     clocks = sampler.stop()
+    best = min(("learned0", "learned1", "learned2"), key=lambda k: res[k]["ms"])
+
+    e2e = None
+    if not args.no_e2e:
+        # the same ratio end to end: g from pinned host memory, phi back to it
+        def e2e_ms(corr, steps=3):
+            stream = torch.cuda.Stream()
+            with pb.PCG(ev["n"], ev["Ls"], torch.from_numpy(a).cuda()) as pcg:
+                gh = torch.from_numpy(g).pin_memory()
+                ph = torch.empty_like(gh).pin_memory()
+                gd = torch.empty(gh.shape, dtype=gh.dtype, device="cuda")
+                phi = torch.zeros_like(gd)
+                with torch.cuda.stream(stream):
+                    for k in range(steps + 1):
+                        if k == 1:
+                            stream.synchronize()
+                            t0 = time.perf_counter()
+                        gd.copy_(gh, non_blocking=True)
+                        if corr is None:
+                            phi.zero_()
+                        else:
+                            pcg.learned_guess(net, phi, gd, corrections=corr, stream=stream)
+                        pcg.solve(phi, gd, tol=ev["tol"], maxit=1000, stream=stream)
+                        ph.copy_(phi, non_blocking=True)
+                    stream.synchronize()
+                return (time.perf_counter() - t0) / steps * 1e3
+
+        plain_ms, learned_ms = e2e_ms(None), e2e_ms(int(best[-1]))
+        e2e = {"value": plain_ms / learned_ms, "unit": "x (speedup, >1 = learned faster)",
+               "plain_ms": plain_ms, "learned_ms": learned_ms,
+               "h2d_bytes_per_step": g.size * 8, "d2h_bytes_per_step": g.size * 8,
+               "path": "g from pinned host memory, PCG solve from zero or from the learned guess, phi to pinned host memory"}
     net.close()
     net64 = learned.load_network(spec["n_train"], theta, **arch)
     held = []
@@ -952,7 +1018,6 @@ def run_learned(args):
         r = solve_set(spec["n_train"], ev["Ls"], a_h, g_h, net64, 2, 1)
         held.append({k: v["iterations"] for k, v in r.items()})
     net64.close()
-    best = min(("learned0", "learned1", "learned2"), key=lambda k: res[k]["ms"])
     line = {
         "metric": "learned PCG: time to 1e-8 relative residual, plain FFT-preconditioned PCG / with the learned guess",
         "value": res["plain"]["ms"] / res[best]["ms"], "unit": "x (speedup, >1 = learned faster)",
@@ -972,7 +1037,7 @@ def run_learned(args):
                      "unit": "GB/s", "frac": fwd_bytes / (fwd_ms / 1e3) / 1e9 / load_peaks()[0], "traffic": None,
                      "kernel": "network forward at 256^3 (all its kernels)",
                      "bytes_per_cell": fwd_bytes / Nc, "peak_source": f"{load_peaks()[1]} hbm_gbs"},
-        "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clocks,
+        "cpu_baseline": None, "e2e": e2e, "gpu_launches": None, "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -76,6 +76,7 @@ struct FastXArgs {
   float2* ws;
   long long g_sy, g_sz;    // element strides of g between y rows and z planes
   long long phi_sy, phi_sz;
+  int stage_g;             // forward, M = 1024: rows of g are 16-byte aligned and staged by bulk copies
   int* err;                // bounded-wait timeout flag
 };
 
@@ -509,18 +510,19 @@ __device__ __forceinline__ void ws_row_of(const FastXArgs& a, long long r, long 
 // back to x_{2m} / x_{2M-1-2m} (DCT-III; DST-III with the odd samples
 // negated).
 //
-// Backward input staging: the CTA's 2 * LPC workspace rows are copied whole
-// into shared memory by the bulk-copy engine (one copy per row, completing
-// on one mbarrier), and the C2R / DCT-III assembly reads them there (R2C:
+// Input staging: the CTA's 2 * LPC rows are copied whole into shared memory
+// by the bulk-copy engine (one copy per row, completing on one mbarrier),
+// and the first step reads them there.  Backward: the workspace rows (R2C:
 // M/2 + 2 complex per row, the row with its first padding element, so that
-// every copy is a multiple of 16 bytes; DCT: M reals).  The staging area is
-// the same memory as the line buffer, so a barrier separates the last
-// staged read from the first line write.  1024^3: 1.87 -> 1.64 ms.  The
-// forward sweep reads g straight into registers (staging it as well was
-// slower: 1.93 -> 2.18 ms at 1024^3).
-template <int M, int KX> struct XStageRow {
-  // elements of 4 bytes per staged backward row
-  static constexpr int value = KX == FX_R2C ? 2 * (M / 2 + 2) : M;
+// every copy is a multiple of 16 bytes; DCT: M reals), 1024^3: 1.87 -> 1.56
+// ms.  Forward: the rows of g (M reals), only for M = 1024 and 16-byte
+// aligned rows (a.stage_g): 1024^3 1.92 -> 1.78 ms, while shorter lines
+// were slower staged (512^3: 0.31 -> 0.34 ms) and read g straight into
+// registers.  The staging area is the same memory as the line buffer, so a
+// barrier separates the last staged read from the first line write.
+template <int M, int MODE, int KX> struct XStageRow {
+  // elements of 4 bytes per staged row
+  static constexpr int value = (MODE == FM_INV && KX == FX_R2C) ? 2 * (M / 2 + 2) : M;
 };
 
 template <int R1, int R2, int MODE, int KX>
@@ -529,8 +531,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 2 : 3) fast_x_kernel(const Fa
   constexpr int RMAX = Shape<R1, R2>::RMAX;
   constexpr int LS = R1 * (R2 + 1);  // padded line stride (complex)
   constexpr int LPC = 256 / RMAX;    // lines per CTA
-  constexpr bool BULK = MODE == FM_INV;
-  constexpr int SR = XStageRow<M, KX>::value;
+  constexpr int SR = XStageRow<M, MODE, KX>::value;
   static_assert(2 * LPC * SR <= 2 * LPC * LS, "staged rows fit in the line buffer");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float2* sm = reinterpret_cast<float2*>(smem_raw);
@@ -548,8 +549,9 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 2 : 3) fast_x_kernel(const Fa
   float sa = 1.f, sb = 1.f;
   if (va) ws_row_of(a, ra, wa, sa);
   if (vb) ws_row_of(a, rb, wb, sb);
+  const bool bulk = MODE == FM_INV || (M == 1024 && a.stage_g);
 
-  if (BULK) {
+  if (bulk) {
     if (tid == 0) {
       mbar_init(bar, 1);
       fence_mbar_init();
@@ -559,10 +561,16 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 2 : 3) fast_x_kernel(const Fa
     if (tid == 0) mbar_arrive_expect_tx(bar, (uint32_t)(nr * SR * 4));
     if (tid < nr) {
       const long long r = r0 + tid;
-      long long wr;
-      float sg;
-      ws_row_of(a, r, wr, sg);
-      bulk_load_1d(stage + (size_t)tid * SR, a.ws + wr * a.ws_ld, (uint32_t)(SR * 4), bar);
+      const void* src;
+      if (MODE == FM_FWD) {
+        src = a.g + (r % a.ny) * a.g_sy + (r / a.ny) * a.g_sz;
+      } else {
+        long long wr;
+        float sg;
+        ws_row_of(a, r, wr, sg);
+        src = a.ws + wr * a.ws_ld;
+      }
+      bulk_load_1d(stage + (size_t)tid * SR, src, (uint32_t)(SR * 4), bar);
     }
     const bool ok = mbar_wait_bounded(bar, 0);
     if (__syncthreads_or(!ok)) {
@@ -572,12 +580,12 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 2 : 3) fast_x_kernel(const Fa
   }
 
   if (MODE == FM_FWD) {
-    // DIF pass 1 straight from global rows a, b
+    // DIF pass 1 from rows a, b (staged, or straight from global memory)
     float2 u[R1];
     const int j = bi;
     if (bi < R2) {
-      const float* ga = a.g + (ra % a.ny) * a.g_sy + (ra / a.ny) * a.g_sz;
-      const float* gb = a.g + (rb % a.ny) * a.g_sy + (rb / a.ny) * a.g_sz;
+      const float* ga = bulk ? stage + (size_t)(2 * l) * SR : a.g + (ra % a.ny) * a.g_sy + (ra / a.ny) * a.g_sz;
+      const float* gb = bulk ? stage + (size_t)(2 * l + 1) * SR : a.g + (rb % a.ny) * a.g_sy + (rb / a.ny) * a.g_sz;
 #pragma unroll
       for (int q = 0; q < R1; q++) {
         const int m = j + R2 * q;
@@ -591,6 +599,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 2 : 3) fast_x_kernel(const Fa
         }
       }
     }
+    if (bulk) __syncthreads();  // the line buffer overwrites the staged rows
     if (bi < R2) {
       Dft<float, R1, false>::run(u);
       if (j != 0) {
