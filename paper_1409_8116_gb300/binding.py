@@ -36,6 +36,7 @@ EXPORTED = [
     "poisfft_plan_create",
     "poisfft_solve",
     "poisfft_solve_host",
+    "poisfft_solve_host_async",
     "poisfft_check",
     "poisfft_destroy",
     "poisfft_status_string",
@@ -100,6 +101,8 @@ def _load():
     lib.poisfft_solve.restype = ctypes.c_int
     lib.poisfft_solve_host.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.poisfft_solve_host.restype = ctypes.c_int
+    lib.poisfft_solve_host_async.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.poisfft_solve_host_async.restype = ctypes.c_int
     lib.poisfft_check.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     lib.poisfft_check.restype = ctypes.c_int
     lib.poisfft_destroy.argtypes = [ctypes.c_void_p]
@@ -239,6 +242,10 @@ def solve_host(plan, phi, g, stream=None):
     return lib.poisfft_solve_host(plan, _ptr(phi), _ptr(g), _stream(stream))
 
 
+def solve_host_async(plan, phi, g, stream=None):
+    return lib.poisfft_solve_host_async(plan, _ptr(phi), _ptr(g), _stream(stream))
+
+
 def solve_noalloc(n, L, bc, approx, dtype, phi, g, stream=None):
     """poisfft_solve_noalloc: one solve with no device allocation (workspace in
     the library's fixed 32 MiB device array).  Returns the status code."""
@@ -318,6 +325,11 @@ class Plan:
         rc = solve_host(self._p, phi, g, stream)
         if rc != OK:
             raise PoisFFTError(rc, "poisfft_solve_host")
+
+    def solve_host_async(self, phi, g, stream=None):
+        rc = solve_host_async(self._p, phi, g, stream)
+        if rc != OK:
+            raise PoisFFTError(rc, "poisfft_solve_host_async")
 
     def check(self, stream=None):
         return check(self._p, stream)

@@ -467,6 +467,16 @@ struct poisfft_plan {
   std::vector<SweepLaunch> sweeps;
   void* stage_g = nullptr;
   void* stage_phi = nullptr;
+  // poisfft_solve_host_async: two staging pairs used in turn, copy streams, events
+  struct HostPipe {
+    bool ready = false;
+    int next = 0;
+    bool used[2] = {false, false};
+    void* g[2] = {nullptr, nullptr};
+    void* phi[2] = {nullptr, nullptr};
+    cudaStream_t in = nullptr, out = nullptr;
+    cudaEvent_t copied_in[2] = {nullptr, nullptr}, solved[2] = {nullptr, nullptr}, copied_out[2] = {nullptr, nullptr};
+  } pipe;
   float* refine_r = nullptr;         // FP32 residual / correction of poisfft_solve_refined
   int refinements = 2;               // POISFFT_MIXED plans: refinement steps of poisfft_solve
   int fused_axis = 0;                // general 3D plans: the strided axis whose sweep divides
@@ -484,6 +494,24 @@ struct poisfft_plan {
 
 namespace {
 
+// Buffers, streams and events of poisfft_solve_host_async (waits for the
+// pipeline's copies first, so that no copy outlives its staging buffer).
+void release_host_pipe(poisfft_plan* p) {
+  auto& q = p->pipe;
+  if (q.in) cudaStreamSynchronize(q.in);
+  if (q.out) cudaStreamSynchronize(q.out);
+  for (int b = 0; b < 2; b++) {
+    if (q.g[b]) cudaFree(q.g[b]);
+    if (q.phi[b]) cudaFree(q.phi[b]);
+    if (q.copied_in[b]) cudaEventDestroy(q.copied_in[b]);
+    if (q.solved[b]) cudaEventDestroy(q.solved[b]);
+    if (q.copied_out[b]) cudaEventDestroy(q.copied_out[b]);
+  }
+  if (q.in) cudaStreamDestroy(q.in);
+  if (q.out) cudaStreamDestroy(q.out);
+  q = poisfft_plan::HostPipe();
+}
+
 void free_plan(poisfft_plan* p) {
   if (!p) return;
   if (p->ws) cudaFree(p->ws);
@@ -497,6 +525,7 @@ void free_plan(poisfft_plan* p) {
   if (p->zm_count) cudaFree(p->zm_count);
   if (p->stage_g) cudaFree(p->stage_g);
   if (p->stage_phi) cudaFree(p->stage_phi);
+  release_host_pipe(p);
   if (p->refine_r) cudaFree(p->refine_r);
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
   for (int i = 0; i < 3; i++) {
@@ -1238,6 +1267,57 @@ int poisfft_solve_host(poisfft_plan* p, void* phi_host, const void* g_host, void
   if (cudaMemcpyAsync(phi_host, p->stage_phi, fb, cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return POISFFT_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return POISFFT_ERR_CUDA;
+  return POISFFT_OK;
+}
+
+int poisfft_solve_host_async(poisfft_plan* p, void* phi_host, const void* g_host, void* stream) {
+  if (!p || !phi_host || !g_host) return POISFFT_ERR_INVALID_ARG;
+  FaultScope fault;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t fb = user_field_bytes(p);
+  auto& q = p->pipe;
+  if (!q.ready) {
+    bool ok = true;
+    for (int b = 0; b < 2 && ok; b++)
+      ok = dev_malloc(&q.g[b], fb) == cudaSuccess && dev_malloc(&q.phi[b], fb) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      release_host_pipe(p);
+      return POISFFT_ERR_ALLOC;
+    }
+    ok = cudaStreamCreateWithFlags(&q.in, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&q.out, cudaStreamNonBlocking) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; b++)
+      ok = cudaEventCreateWithFlags(&q.copied_in[b], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&q.solved[b], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&q.copied_out[b], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      release_host_pipe(p);
+      return POISFFT_ERR_CUDA;
+    }
+    q.ready = true;
+  }
+  const int b = q.next;
+  // input copy into staging pair b, once the solve of two calls ago has read it
+  if (q.used[b] && cudaStreamWaitEvent(q.in, q.solved[b], 0) != cudaSuccess) return POISFFT_ERR_CUDA;
+  if (cudaMemcpyAsync(q.g[b], g_host, fb, cudaMemcpyHostToDevice, q.in) != cudaSuccess ||
+      cudaEventRecord(q.copied_in[b], q.in) != cudaSuccess)
+    return POISFFT_ERR_CUDA;
+  // the solve on the caller's stream: after the input copy, and after the
+  // result copy of two calls ago has read staging field phi[b]
+  if (cudaStreamWaitEvent(st, q.copied_in[b], 0) != cudaSuccess) return POISFFT_ERR_CUDA;
+  if (q.used[b] && cudaStreamWaitEvent(st, q.copied_out[b], 0) != cudaSuccess) return POISFFT_ERR_CUDA;
+  int rc = poisfft_solve(p, q.phi[b], q.g[b], stream);
+  if (rc != POISFFT_OK) return rc;
+  if (cudaEventRecord(q.solved[b], st) != cudaSuccess) return POISFFT_ERR_CUDA;
+  // result copy; the caller's stream completes with it
+  if (cudaStreamWaitEvent(q.out, q.solved[b], 0) != cudaSuccess ||
+      cudaMemcpyAsync(phi_host, q.phi[b], fb, cudaMemcpyDeviceToHost, q.out) != cudaSuccess ||
+      cudaEventRecord(q.copied_out[b], q.out) != cudaSuccess || cudaStreamWaitEvent(st, q.copied_out[b], 0) != cudaSuccess)
+    return POISFFT_ERR_CUDA;
+  q.used[b] = true;
+  q.next = b ^ 1;
   return POISFFT_OK;
 }
 

@@ -83,6 +83,7 @@ def test_dims_out_of_range(pb):
 def test_null_plan_calls(pb):
     assert pb.lib.poisfft_solve(None, None, None, None) == pb.ERR_INVALID_ARG
     assert pb.lib.poisfft_solve_host(None, None, None, None) == pb.ERR_INVALID_ARG
+    assert pb.lib.poisfft_solve_host_async(None, None, None, None) == pb.ERR_INVALID_ARG
     assert pb.lib.poisfft_check(None, None) == pb.ERR_INVALID_ARG
     assert pb.lib.poisfft_destroy(None) == pb.OK
     info = (ctypes.c_int64 * 4)()
