@@ -378,12 +378,12 @@ def run_ours(args):
         # consecutive steps overlap one step's result copy with the next input)
         for _ in range(max(1, args.warmup)):
             plan.solve_host_async(ph, gh, stream)
-        stream.synchronize()
+        assert plan.check(stream) == pb.OK
         barrier()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             plan.solve_host_async(ph, gh, stream)
-        stream.synchronize()
+        assert plan.check(stream) == pb.OK  # waits for the last result copy too
         t_e2e = reduce_max(time.perf_counter() - t0, world, "cuda")
         e2e_value = throughput(npts, e2e_steps, world, t_e2e)
         # the synchronous call (one solve at a time), for comparison
@@ -457,7 +457,7 @@ def run_ours(args):
                 "value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": npts * esize,
                 "d2h_bytes_per_step": npts * esize,
                 "path": "poisfft_solve_host_async: pinned host buffers, one copy each way through two alternating "
-                        "device staging pairs, K calls then one stream synchronisation",
+                        "device staging pairs, K calls then poisfft_check (waits for the last result copy)",
                 "synchronous_call_value": e2e_sync, "equals_device_result": e2e_same},
             "gpu_launches": len(launches) * args.steps,
             "clocks": clocks,

@@ -139,21 +139,24 @@ int poisfft_solve_host(poisfft_plan* plan, void* phi_host, const void* g_host, v
 /* The host-buffer solve without waiting, for many right-hand sides in a row.
  * Enqueues the copy of g_host to the device (on an internal copy stream),
  * the solve (on `stream`) and the copy of the result to phi_host (on a
- * second internal copy stream), makes `stream` wait for that last copy, and
- * returns.  The plan uses two staging pairs in turn, so one call's result
- * copy runs while the next call's input copy and solve proceed, and the two
- * directions of the CPU-GPU link work at once.  Neither host buffer may be
- * touched until `stream` has been synchronised (poisfft_check does that);
- * pinned host buffers are needed for the copies to overlap.  Staging (four
- * fields) is allocated on the first call and kept until poisfft_destroy.
- * Same status codes as poisfft_solve; POISFFT_ERR_ALLOC if staging cannot
- * be allocated.  The paper has no counterpart (Sec. 3 describes one solve
- * call on caller-owned arrays). */
+ * second internal copy stream), and returns.  The plan uses two staging
+ * pairs in turn, so one call's result copy runs while the next call's input
+ * copy and solve proceed, and the two directions of the CPU-GPU link work at
+ * once.  `stream` is made to wait for the PREVIOUS call's result copy, so
+ * synchronising it completes every call but the last; poisfft_check(plan,
+ * stream) waits for the last result copy as well.  No host buffer of a call
+ * may be touched until poisfft_check has returned; pinned host buffers are
+ * needed for the copies to overlap.  Staging (four fields) is allocated on
+ * the first call and kept until poisfft_destroy.  Same status codes as
+ * poisfft_solve; POISFFT_ERR_ALLOC if staging cannot be allocated.  The
+ * paper has no counterpart (Sec. 3 describes one solve call on caller-owned
+ * arrays). */
 int poisfft_solve_host_async(poisfft_plan* plan, void* phi_host, const void* g_host, void* stream);
 
 /* Read and clear the plan's device error flag (bounded waits in the kernels
- * set it instead of hanging).  Synchronises `stream`.  Returns POISFFT_OK,
- * POISFFT_ERR_TIMEOUT or POISFFT_ERR_CUDA. */
+ * set it instead of hanging).  Synchronises `stream` and the result copies of
+ * poisfft_solve_host_async.  Returns POISFFT_OK, POISFFT_ERR_TIMEOUT or
+ * POISFFT_ERR_CUDA. */
 int poisfft_check(poisfft_plan* plan, void* stream);
 
 /* Release the plan's device memory and tables.  NULL is a no-op.  The caller

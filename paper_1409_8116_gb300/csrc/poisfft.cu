@@ -1311,11 +1311,15 @@ int poisfft_solve_host_async(poisfft_plan* p, void* phi_host, const void* g_host
   int rc = poisfft_solve(p, q.phi[b], q.g[b], stream);
   if (rc != POISFFT_OK) return rc;
   if (cudaEventRecord(q.solved[b], st) != cudaSuccess) return POISFFT_ERR_CUDA;
-  // result copy; the caller's stream completes with it
+  // result copy.  The caller's stream follows the previous call's result
+  // copy, not this one, so that the next call's solve can run beside it; at
+  // most one result copy is in flight beyond the stream, and poisfft_check
+  // waits for it.
   if (cudaStreamWaitEvent(q.out, q.solved[b], 0) != cudaSuccess ||
       cudaMemcpyAsync(phi_host, q.phi[b], fb, cudaMemcpyDeviceToHost, q.out) != cudaSuccess ||
-      cudaEventRecord(q.copied_out[b], q.out) != cudaSuccess || cudaStreamWaitEvent(st, q.copied_out[b], 0) != cudaSuccess)
+      cudaEventRecord(q.copied_out[b], q.out) != cudaSuccess)
     return POISFFT_ERR_CUDA;
+  if (q.used[b ^ 1] && cudaStreamWaitEvent(st, q.copied_out[b ^ 1], 0) != cudaSuccess) return POISFFT_ERR_CUDA;
   q.used[b] = true;
   q.next = b ^ 1;
   return POISFFT_OK;
@@ -1325,6 +1329,8 @@ int poisfft_check(poisfft_plan* p, void* stream) {
   if (!p) return POISFFT_ERR_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (cudaStreamSynchronize(st) != cudaSuccess) return POISFFT_ERR_CUDA;
+  // the last result copy of poisfft_solve_host_async
+  if (p->pipe.ready && cudaStreamSynchronize(p->pipe.out) != cudaSuccess) return POISFFT_ERR_CUDA;
   int h = 0;
   if (cudaMemcpy(&h, p->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return POISFFT_ERR_CUDA;
   if (h != 0) {
