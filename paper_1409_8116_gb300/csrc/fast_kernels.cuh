@@ -620,7 +620,46 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 2 : 3) fast_x_kernel(const Fa
       for (int s = 0; s < R2; s++) line[b * (R2 + 1) + s] = y[s];
     }
     __syncthreads();
-    if (KX == FX_R2C) {
+    if (KX == FX_R2C && M == 1024) {
+      // split Z into the half spectra of rows a and b, staged in shared memory
+      // (M/2 + 2 complex per row: the row and its first padding element, set
+      // to zero) and written back by one bulk copy per row
+      constexpr int NH = M / 2 + 1, OW = M / 2 + 2, NK = (NH + RMAX - 1) / RMAX;
+      float2 A[NK], B[NK];
+#pragma unroll
+      for (int i = 0; i < NK; i++) {
+        const int k = bi + i * RMAX;
+        if (k < NH) {
+          const float2 z1 = line[xpos<R1, R2>(k)];
+          const float2 z2 = line[xpos<R1, R2>(k == 0 ? 0 : M - k)];
+          A[i] = make_float2(sa * 0.5f * (z1.x + z2.x), sa * 0.5f * (z1.y - z2.y));
+          B[i] = make_float2(sb * 0.5f * (z1.y + z2.y), sb * 0.5f * (z2.x - z1.x));
+        }
+      }
+      __syncthreads();  // the staged rows overwrite the line buffer
+      float2* oa = sm + (size_t)(2 * l) * OW;
+      float2* ob = oa + OW;
+#pragma unroll
+      for (int i = 0; i < NK; i++) {
+        const int k = bi + i * RMAX;
+        if (k < NH) {
+          oa[k] = A[i];
+          ob[k] = B[i];
+        }
+      }
+      if (bi == 0) oa[NH] = ob[NH] = make_float2(0.f, 0.f);
+      fence_proxy_async();
+      __syncthreads();
+      const int nr = (int)(a.nrows - r0 < 2 * LPC ? a.nrows - r0 : 2 * LPC);
+      if (tid < nr) {
+        long long wr;
+        float sg;
+        ws_row_of(a, r0 + tid, wr, sg);
+        bulk_store_1d(a.ws + wr * a.ws_ld, sm + (size_t)tid * OW, (uint32_t)(OW * 8));
+        bulk_commit_group();
+        bulk_wait_group_read0();
+      }
+    } else if (KX == FX_R2C) {
       // split Z into the half spectra of rows a and b
       constexpr int NH = M / 2 + 1;
       float2* da = a.ws + wa * a.ws_ld;

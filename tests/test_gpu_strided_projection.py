@@ -34,6 +34,9 @@ def pb():
 @pytest.mark.parametrize("n,bcs,dtype,tol", [
     ((64, 64, 64), (W.P, W.P, W.NS), "f32", 1e-5),          # specialised kernels
     ((256, 64, 128), (W.P, W.DS, W.NS), "f32", 1e-5),       # specialised kernels
+    # 1024-point x lines: dense rows of g are staged by bulk copies, these
+    # ghost-cell rows start off a 16-byte boundary and take the direct loads
+    ((1024, 64, 64), (W.P, W.P, W.NS), "f32", 1e-5),
     ((33, 20, 17), (W.DR, W.NR, W.P), "f64", 1e-12),        # general kernels + pair divide
     ((45, 27, 21), (W.P, W.DS, W.NR), "f64", 1e-12),        # general kernels
     ((50, 40), (W.P, W.NS), "f32", 1e-5),
