@@ -77,6 +77,7 @@ struct FastXArgs {
   long long g_sy, g_sz;    // element strides of g between y rows and z planes
   long long phi_sy, phi_sz;
   int stage_g;             // forward, M = 1024: rows of g are 16-byte aligned and staged by bulk copies
+  int stage_phi;           // backward, M = 1024: rows of phi are 16-byte aligned and written by bulk copies
   int* err;                // bounded-wait timeout flag
 };
 
@@ -750,7 +751,50 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 2 : 3) fast_x_kernel(const Fa
       for (int s = 0; s < R2; s++) line[b * (R2 + 1) + s] = y[s];
     }
     __syncthreads();
-    if (bi < R2) {
+    if (M == 1024 && a.stage_phi) {
+      // rows a, b of phi staged in shared memory (M reals each, over the line
+      // buffer) and written back by one bulk copy per row
+      float2 u[R1];
+      const int j = bi;
+      if (bi < R2) {
+#pragma unroll
+        for (int q = 0; q < R1; q++) u[q] = line[q * (R2 + 1) + j];
+        if (j != 0) {
+#pragma unroll
+          for (int q = 1; q < R1; q++) u[q] = cmulc<float>(u[q], __ldg(&a.tw[q * R2 + j]));
+        }
+        Dft<float, R1, true>::run(u);
+      }
+      __syncthreads();  // the staged rows overwrite the line buffer
+      if (bi < R2) {
+        float* oa = stage + (size_t)(2 * l) * M;
+        float* ob = oa + M;
+#pragma unroll
+        for (int s = 0; s < R1; s++) {
+          const int n = j + R2 * s;
+          if (KX == FX_R2C) {
+            oa[n] = u[s].x;
+            ob[n] = u[s].y;
+          } else {
+            const bool odd = s >= R1 / 2;  // n >= M/2
+            const int dst = odd ? 2 * M - 1 - 2 * n : 2 * n;
+            const float sg = (odd && a.xsign) ? -1.f : 1.f;
+            oa[dst] = sg * u[s].x;
+            ob[dst] = sg * u[s].y;
+          }
+        }
+      }
+      fence_proxy_async();
+      __syncthreads();
+      const int nr = (int)(a.nrows - r0 < 2 * LPC ? a.nrows - r0 : 2 * LPC);
+      if (tid < nr) {
+        const long long r = r0 + tid;
+        bulk_store_1d(a.phi + (r % a.ny) * a.phi_sy + (r / a.ny) * a.phi_sz, stage + (size_t)tid * M,
+                      (uint32_t)(M * 4));
+        bulk_commit_group();
+        bulk_wait_group_read0();
+      }
+    } else if (bi < R2) {
       const int j = bi;
       float2 u[R1];
 #pragma unroll

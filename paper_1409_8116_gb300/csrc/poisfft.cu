@@ -922,6 +922,7 @@ int enqueue(poisfft_plan* p, void* phi, const void* g, cudaStream_t st, const Fi
       a.phi_sz = fs.phi_sz;
       // whole-row bulk copies need 16-byte aligned row starts
       a.stage_g = (uintptr_t)g % 16 == 0 && fs.g_sy % 4 == 0 && fs.g_sz % 4 == 0;
+      a.stage_phi = (uintptr_t)phi % 16 == 0 && fs.phi_sy % 4 == 0 && fs.phi_sz % 4 == 0;
       e = launch_fast_x(L.M, L.fmode, L.fkind, a, L.grid, L.smem, st);
     } else if (L.tc) {
       tc::TcStridedArgs ta;
