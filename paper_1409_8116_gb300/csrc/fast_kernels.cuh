@@ -102,6 +102,29 @@ struct Shape {
 // shifts consecutive blocks across the smem banks for narrow tiles.
 template <int W> struct BlockPad { static constexpr int value = W < 8 ? W : 8; };
 
+// Write the tile staged in shared memory in the TMA box layout (row * W +
+// column) back with tensor stores, one per box; called by every thread of
+// the CTA (the fence and barrier make the staged values visible to the copy
+// engine), thread 0 issues the stores and waits until they have read the
+// tile.
+template <int W>
+__device__ __forceinline__ void store_tile(const CUtensorMap& tmap, const FastStridedArgs& a, const float2* sm,
+                                           int c0, int outer) {
+  fence_proxy_async();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < a.nbox; b++) {
+      const float2* src = sm + (size_t)b * a.box_h * W;
+      if (a.axis_dim == 1)
+        tma_store_3d(&tmap, src, 2 * c0, b * a.box_h, outer);
+      else
+        tma_store_3d(&tmap, src, 2 * c0, outer, b * a.box_h);
+    }
+    bulk_commit_group();
+    bulk_wait_group_read0();
+  }
+}
+
 template <int R1, int R2, int W, int MODE, int KIND>
 __global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, 768 / (W * Shape<R1, R2>::RMAX))
     fast_strided_kernel(const __grid_constant__ CUtensorMap tmap, const FastStridedArgs a) {
@@ -186,6 +209,30 @@ __global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, 768 / (W * Shape<R1, 
       __syncthreads();
     }
 
+    if (M == 1024) {
+      // 1024-point lines: the output tile goes back through shared memory in
+      // the TMA box layout and out by tensor stores (columns beyond the
+      // valid ones are clipped by the tensor map)
+      if (act2) {
+#pragma unroll
+        for (int s2 = 0; s2 < R2; s2++) {
+          const int k = b + R1 * s2;
+          if (DCT) {
+            const int kp = k == 0 ? 0 : M - k;
+            const float2 yp = sm[(kp % R1) * BS + (kp / R1) * W + c];
+            const float2 w = __ldg(&a.mk[k]);
+            y[s2] = cadd<float>(cmul<float>(w, y[s2]), cmulc<float>(yp, w));  // X_k = w Y_k + conj(w) Y_{M-k}
+          }
+        }
+      }
+      __syncthreads();  // the staged output overwrites the coefficients
+      if (act2) {
+#pragma unroll
+        for (int s2 = 0; s2 < R2; s2++) sm[(b + R1 * s2) * W + c] = y[s2];
+      }
+      store_tile<W>(tmap, a, sm, c0, outer);
+      return;
+    }
     if (act2 && col_ok) {
 #pragma unroll
       for (int s2 = 0; s2 < R2; s2++) {
@@ -229,7 +276,26 @@ __global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, 768 / (W * Shape<R1, 
   }
 
   // ---- DIT pass B (radix R1): natural-order output j + R2*s
-  {
+  if (M == 1024) {
+    // staged in shared memory and written by tensor stores (see above)
+    float2 u[R1];
+    const int j = bi;
+    if (bi < R2) {
+#pragma unroll
+      for (int q = 0; q < R1; q++) u[q] = sm[q * BS + j * W + c];
+      if (j != 0) {
+#pragma unroll
+        for (int q = 1; q < R1; q++) u[q] = cmulc<float>(u[q], __ldg(&a.tw[q * R2 + j]));
+      }
+      Dft<float, R1, true>::run(u);
+    }
+    __syncthreads();  // the staged output overwrites the padded tile
+    if (bi < R2) {
+#pragma unroll
+      for (int s = 0; s < R1; s++) sm[(j + R2 * s) * W + c] = u[s];
+    }
+    store_tile<W>(tmap, a, sm, c0, outer);
+  } else {
     float2 u[R1];
     const int j = bi;
     if (bi < R2 && col_ok) {
@@ -465,6 +531,24 @@ __global__ void __launch_bounds__(W * Shape<R1, R2>::RMAX, 768 / (W * Shape<R1, 
   __syncthreads();
 
   // ---- DIT pass B (radix R1): natural-order output j + R2*s
+  if (M == 1024) {
+    // 1024-point lines: staged in the TMA box layout, written by tensor stores
+    float2 u[R1];
+    const int j = bi;
+    if (bi < R2) {
+#pragma unroll
+      for (int q = 0; q < R1; q++) u[q] = sm[bpos(q, j)];
+      if (j != 0) apply_pass_twiddles<R1, R2, true>(u, a.tw, j);
+      Dft<float, R1, true>::run(u);
+    }
+    __syncthreads();  // the staged output overwrites the tile
+    if (bi < R2) {
+#pragma unroll
+      for (int s = 0; s < R1; s++) sm[(j + R2 * s) * W + c] = u[s];
+    }
+    store_tile<W>(tmap, a, sm, c0, outer);
+    return;
+  }
   float2* out = a.data + (size_t)outer * a.s_outer + c0;
   if (bi < R2 && c0 + c < a.ncols) {
     float2 u[R1];
