@@ -289,7 +289,8 @@ def test_fast_path_3d_x_cosine_sine(pb, n, bcs):
 
 
 @pytest.mark.parametrize("n,bcs,approx", [((256, 512), (W.NS, W.DS), W.SPECTRAL), ((1024, 64), (W.DS, W.NS), W.FD2),
-                                          ((64, 64), (W.NS, W.NS), W.FD2), ((512, 128), (W.DS, W.DS), W.SPECTRAL)])
+                                          ((64, 64), (W.NS, W.NS), W.FD2), ((512, 128), (W.DS, W.DS), W.SPECTRAL),
+                                          ((64, 1024), (W.NS, W.DS), W.FD2)])
 def test_fast_path_2d_x_cosine_sine(pb, n, bcs, approx):
     check(pb, tuple(reversed(n)), bcs, approx, "f32", seed=16, method="fft")
 
