@@ -1531,10 +1531,11 @@ struct Fd2Axis {
 };
 
 // phi_{i-1} + phi_{i+1} along one axis with the ghost values of its BC
-// (0 for an absent axis, whose weight is 0)
+// (0 for an absent axis, whose weight is 0; an axis of one point takes both
+// neighbours from the BC: 2 phi_0 for P and NS, -2 phi_0 for DS, 0 for DR)
 __device__ __forceinline__ double fd2_pair(const double* __restrict__ phi, long long idx, int i, const Fd2Axis& a,
                                            double c) {
-  if (a.n == 1) return 0.0;
+  if (a.w == 0.0) return 0.0;
   double l, r;
   if (i > 0) {
     l = phi[idx - a.s];

@@ -39,6 +39,7 @@ CASES = [
     ((64, 128, 64), (W.NS, W.DS, W.NS)),     # specialised kernels, x DCT
     ((40, 300), (W.DR, W.P)),                # 2D
     ((97,), (W.NS,)),                        # 1D singular
+    ((16, 12, 1), (W.P, W.DS, W.NS)),        # z of one point (residual takes both neighbours from the BC)
 ]
 
 
